@@ -1,0 +1,479 @@
+"""Benchmark of the permanent path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one graph-captured persistent forward over the ragged batch of
+65536 permanents (n ~ U{4..20}, row/column multiplicities with parts in
+{1,2,3}, each a submatrix of its own Haar unitary of size 2n), with the
+batch resident in HBM and L2 flushed before every step.  The metric is
+Gray-code terms per second (every permanent counts the exact number of terms
+of the side its Gray code sums); permanents/s, the plain one-launch-per-
+permanent path on the same batch, the single n = 30 permanent, the batched
+boson-sampling workload and the Clements-mesh forward+backward workload are
+reported in the same JSON line under "extra".
+
+``--impl reference`` times the CPU oracle (Ryser's formula in FP64 with
+double-double accumulation, all host cores) on a bounded sample of the same
+batch and prints the same line with "impl": "reference".
+
+Under torchrun (N > 1) every rank runs the whole batch on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints the line with the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gray-code terms/sec & permanents/sec (FP64 roofline %), batched vs plain, 1 GB300"
+UNIT = "terms/s"
+WORKLOAD = ("ragged batch: 65536 permanents, n ~ U{4..20}, row/col multiplicities with parts "
+            "in {1,2,3}, submatrices of per-item Haar 2n x 2n unitaries (seed 1004)")
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, NVIDIA's figure
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "glynn_fwd_persistent_ragged65536.md")
+KERNEL_SOURCES = ["paper_2403_04006_gb300/csrc/glynn_fwd.cu",
+                  "paper_2403_04006_gb300/csrc/pq_device.cuh",
+                  "paper_2403_04006_gb300/csrc/pq_internal.h"]
+
+
+# ---------------------------------------------------------------- distributed helpers
+def rank_env():
+    """(rank, world_size, local_rank) from the torchrun environment."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_dist(backend: str):
+    import torch.distributed as dist
+    rank, world, _ = rank_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pq_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the persistent forward kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    text = open(PROFILE_SUMMARY).read()
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not m or not b or m.group(1) != kernel_hash():
+        return None
+    return float(b.group(1))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(pb, target_ryser_terms: float):
+    """Items of the batch taken with a fixed stride until the oracle's Ryser
+    term count reaches the target: a bounded, representative sample."""
+    order = list(range(0, pb.batch, 7)) + [b for b in range(pb.batch) if b % 7]
+    picked, tot = [], 0.0
+    for b in order:
+        r = pb.row_mult[pb.row_off[b]:pb.row_off[b] + pb.k[b]]
+        tot += float(np.prod(r.astype(np.float64) + 1.0))
+        picked.append(b)
+        if tot >= target_ryser_terms:
+            break
+    return sorted(picked)
+
+
+def glynn_terms(pb, idx) -> int:
+    """Gray-code terms of the cheaper side of each item (the count the GPU sums)."""
+    def side(m):
+        m = [int(x) for x in m if x > 0]
+        if not m:
+            return 0
+        f = int(np.argmin(m))
+        return math.prod(x if i == f else x + 1 for i, x in enumerate(m))
+    tot = 0
+    for b in idx:
+        r = pb.row_mult[pb.row_off[b]:pb.row_off[b] + pb.k[b]]
+        c = pb.col_mult[pb.col_off[b]:pb.col_off[b] + pb.l[b]]
+        tot += min(side(r), side(c))
+    return tot
+
+
+def run_oracle_sample(pb, idx, threads):
+    import oracle as O
+    sub = pb.subset(idx)
+    t0 = time.perf_counter()
+    O.perm_batch(sub.mats, sub.mat_off, sub.k, sub.l, sub.row_mult, sub.row_off, sub.col_mult,
+                 sub.col_off, gold=False, nthreads=threads)
+    return time.perf_counter() - t0
+
+
+# ---------------------------------------------------------------- our arm
+def bench_ours(args):
+    import torch
+
+    from paper_2403_04006_gb300 import api, pq
+    from paper_2403_04006_gb300 import workloads as W
+
+    rank, world, local = rank_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    init_dist("nccl")
+    pq.load_library()
+
+    pb = W.ragged()
+    db = api.DeviceBatch(pb, dev)
+    plan = api.Plan.for_batch(pb, method="batched", use_graph=True)
+    plan.autotune(db)
+    st = plan.stats()
+    out = torch.empty(pb.batch, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    def step():
+        api.permanent_batched(db, plan, out=out, stream=stream)
+
+    # measured FP64 rate of this GPU (roofline denominator)
+    with torch.cuda.stream(stream):
+        pass
+    peak_flops, _ = api.probe_fp64_peak(1 << 16, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step()
+    stream.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(dev)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        t_wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(1.0)  # L2 flush, outside the events
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+        stream.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        barrier(dev)
+        torch.cuda.synchronize(dev)
+    clk = clocks.summary()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_mean = sum(step_ms) / len(step_ms)
+    ms_max = max_over_ranks(ms_mean, dev)
+    value = whole_job_rate(st["terms"], world, ms_max * 1e-3)
+    perms_per_s = whole_job_rate(st["permanents"], world, ms_max * 1e-3)
+    achieved_tflops = st["flops_forward"] / (ms_mean * 1e-3) / 1e12
+
+    # ---- end to end through the C ABI with host buffers
+    host = {k: torch.from_numpy(getattr(pb, k)).pin_memory()
+            for k in ("mats", "mat_off", "k", "l", "row_mult", "row_off", "col_mult", "col_off")}
+    out_host = torch.empty(pb.batch, dtype=torch.complex128).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = out_host.numel() * out_host.element_size()
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for k, t in host.items():
+                getattr(db, k).copy_(t, non_blocking=True)
+            api.permanent_batched(db, plan, out=out, stream=stream)
+            out_host.copy_(out, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), dev)
+    e2e_value = whole_job_rate(st["terms"], world, e2e_s)
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = extra_measurements(args, dev, stream, flush)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = host_cores()
+        idx = oracle_sample(pb, args.cpu_sample_terms)
+        secs = run_oracle_sample(pb, idx, threads)
+        cpu = {"value": glynn_terms(pb, idx) / secs, "unit": UNIT, "cores": threads,
+               "kind": "oracle",
+               "sample": f"{len(idx)} of {pb.batch} permanents (stride-7 order), {secs:.1f} s, "
+                         f"Ryser FP64 + double-double accumulation, {cpu_model()}"}
+
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "permanents": st["permanents"], "terms": st["terms"],
+                   "method": "batched persistent kernel, CUDA graph, autotuned chunks",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"dp{world} (independent batches, no collective)"},
+        "permanents_per_s": perms_per_s,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops,
+                     "peak": peak_flops / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / (peak_flops / 1e12), "traffic": traffic,
+                     "peak_source": "FP64 DFMA probe (pq_probe_fp64_peak) measured in this run",
+                     "peak_nominal": FP64_NOMINAL_TFLOPS,
+                     "frac_of_nominal": achieved_tflops / FP64_NOMINAL_TFLOPS,
+                     "flops_per_step": st["flops_forward"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * int(st["launches_forward"]),
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+        "cpu_baseline": cpu,
+        "extra": extra,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def extra_measurements(args, dev, stream, flush):
+    """Secondary numbers of the same path, one JSON object each."""
+    import torch
+
+    from paper_2403_04006_gb300 import api
+    from paper_2403_04006_gb300 import workloads as W
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        with torch.cuda.stream(stream):
+            fn()
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    res = {}
+    # plain path on the same ragged batch
+    pb = W.ragged()
+    db = api.DeviceBatch(pb, dev)
+    plan_p = api.Plan.for_batch(pb, method="plain")
+    out = torch.empty(pb.batch, dtype=torch.complex128, device=dev)
+    st = plan_p.stats()
+    ms = timed(lambda: api.permanent_batched(db, plan_p, out=out, stream=stream), 3)
+    res["ragged_plain"] = {"terms_per_s": st["terms"] / ms * 1e3,
+                           "permanents_per_s": st["permanents"] / ms * 1e3, "ms": ms,
+                           "launches": st["launches_forward"]}
+    plan_b = api.Plan.for_batch(pb, method="batched")
+    gout = torch.ones(pb.batch, dtype=torch.complex128, device=dev)
+    stb = plan_b.stats()
+    ms = timed(lambda: api.permanent_backward(db, gout, plan_b, stream=stream), 3)
+    res["ragged_backward_batched"] = {"terms_per_s": stb["terms"] / ms * 1e3, "ms": ms,
+                                      "tflops": stb["flops_backward"] / ms / 1e9}
+    del db, plan_p, plan_b
+    # single n = 30
+    A = W.single_large(30)
+    pb30 = W.pack_batch([(A, [1] * 30, [1] * 30)])
+    db30 = api.DeviceBatch(pb30, dev)
+    plan30 = api.Plan.for_batch(pb30)
+    out30 = torch.empty(1, dtype=torch.complex128, device=dev)
+    st = plan30.stats()
+    ms = timed(lambda: api.permanent_batched(db30, plan30, out=out30, stream=stream), 3)
+    res["single_n30"] = {"terms_per_s": st["terms"] / ms * 1e3, "ms": ms,
+                         "tflops": st["flops_forward"] / ms / 1e9}
+    # batched boson sampling, m = 24, 4096 patterns
+    U, s, t = W.bs_batched()
+    Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))
+    for method in ("batched", "plain"):
+        plan = api.Plan.for_bs(24, s, t, method=method, use_graph=(method == "batched"))
+        st = plan.stats()
+        ms = timed(lambda: api.bs_probs(Ud, sd, td, plan, stream=stream), 10)
+        res[f"bs_m24_{method}"] = {"terms_per_s": st["terms"] / ms * 1e3,
+                                   "permanents_per_s": st["permanents"] / ms * 1e3, "ms": ms}
+    # Clements mesh -> probabilities -> sum -> backward, m = 16, 1024 patterns
+    th, ph, s5, t5 = W.gradient_workload()
+    thd = torch.from_numpy(th).to(dev).requires_grad_(True)
+    phd = torch.from_numpy(ph).to(dev).requires_grad_(True)
+    sd5, td5 = torch.from_numpy(s5).to(dev), torch.from_numpy(t5).to(dev)
+    plan5 = api.Plan.for_bs(16, s5, t5)
+
+    def step5():
+        U5 = api.ClementsMesh.apply(thd, phd, 16)
+        api.BSProbs.apply(U5, sd5, td5, plan5).sum().backward()
+
+    ms = timed(step5, 10)
+    res["gradient_m16"] = {"ms_fwd_bwd": ms, "terms": plan5.stats()["terms"]}
+    return res
+
+
+# ---------------------------------------------------------------- reference arm
+def bench_reference(args):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return  # the CPU oracle runs once, on rank 0
+    from paper_2403_04006_gb300 import workloads as W
+    import oracle as O
+    O.build()
+    pb = W.ragged()
+    threads = host_cores()
+    idx = oracle_sample(pb, args.cpu_sample_terms)
+    terms = glynn_terms(pb, idx)
+    for _ in range(args.warmup):
+        run_oracle_sample(pb, idx[: max(1, len(idx) // 8)], threads)
+    secs = [run_oracle_sample(pb, idx, threads) for _ in range(args.steps)]
+    per = sum(secs) / len(secs)
+    value = terms / per
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample_permanents": len(idx), "sample_terms": terms},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{len(idx)} of {pb.batch} permanents per step, "
+                                   f"Ryser FP64 + double-double accumulation, {cpu_model()}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="skip the extra measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-terms", type=float, default=1.5e8,
+                    help="Ryser terms of the oracle sample (about 10-30 s on the host)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

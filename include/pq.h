@@ -1,0 +1,261 @@
+/*
+ * pq.h -- C ABI of the GB300 (sm_103a) permanent library.
+ *
+ * The library evaluates permanents of matrices with repeated rows and columns
+ * and the boson-sampling output probabilities built on them, with their
+ * gradients, on one GPU.  Paper: "Piquasso: A Photonic Quantum Computer
+ * Simulation Software Platform", arXiv 2403.04006.
+ *
+ *   per(A) = sum_{sigma in S_n} prod_i A[sigma(i)][i]            Eq. (per_def)
+ *   p(s,t) = |per(U_{s,t})|^2 / (prod_i t_i! prod_i s_i!)        Eq. (BS_prob)
+ *
+ * A is given by a k x l base matrix B and multiplicities r (rows), c (columns)
+ * with sum r = sum c = n: A repeats base row i r_i times and base column j c_j
+ * times ("row or column multiplicities", Sec. 4.2 "Boson Sampling").  The GPU
+ * evaluates the Balasubramanian-Bax-Franklin-Glynn (BB/FG) formula extended to
+ * multiplicities with a mixed-radix ("n-ary") Gray code whose digit for row i
+ * runs over the number of sign flips among its r_i copies (Sec. 4.2).
+ *
+ * Conventions shared by every call:
+ *  - Complex numbers are pq_c128 = {re, im}, 16 bytes, interleaved; the layout
+ *    of torch.complex128 / std::complex<double>.
+ *  - Matrices are dense row-major.  In the boson-sampling calls U is m x m and
+ *    indexed U[out][in]: U_{s,t} takes the rows of the output modes (repeated
+ *    t_i times) and the columns of the input modes (repeated s_j times).
+ *    |per|^2 does not change under transposition, so probabilities do not
+ *    depend on this choice; gradient layouts do.
+ *  - Pointers documented "device" must point to device memory of the current
+ *    CUDA device; "host" pointers to host memory.  The caller owns every buffer
+ *    it passes; the library never frees caller memory and keeps no pointer to
+ *    it after the call returns (except inside a plan, see below).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls are asynchronous with respect to the host unless stated.
+ *  - Return value: PQ_OK (0) or a negative PQ_ERR_* code; pq_last_error()
+ *    gives a message for the calling thread.  Nothing aborts and nothing
+ *    throws across this boundary.  Argument errors are detected on the host
+ *    before any launch.
+ *  - Gradients follow PyTorch's convention for complex tensors: for a real
+ *    loss L, grad_z = dL/dRe z + i dL/dIm z; for a holomorphic f,
+ *    grad_in = grad_out * conj(df/dz).
+ *  - Limits: n <= PQ_MAX_N photons, base dimensions k, l <= PQ_MAX_DIM, and on
+ *    the side that is not summed at most PQ_MAX_PRODUCT_COLS distinct columns;
+ *    term counts below 2^62.  Larger inputs return PQ_ERR_UNSUPPORTED.
+ */
+#ifndef PQ_GB300_H
+#define PQ_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PQ_OK 0
+#define PQ_ERR_ARG (-1)         /* null pointer, negative size, sum r != sum c, ... */
+#define PQ_ERR_UNSUPPORTED (-2) /* beyond the limits below                          */
+#define PQ_ERR_CUDA (-3)        /* a CUDA runtime call failed                       */
+#define PQ_ERR_TIMEOUT (-4)     /* a bounded device wait gave up                    */
+#define PQ_ERR_NOMEM (-5)       /* host or device allocation failed                 */
+#define PQ_ERR_STATE (-6)       /* plan used with data it was not made for          */
+
+#define PQ_MAX_N 48
+#define PQ_MAX_DIM 64
+#define PQ_MAX_PRODUCT_COLS 40
+
+typedef struct { double re, im; } pq_c128;
+
+/* Ragged batch of base matrices; every pointer is a DEVICE pointer.
+ * Item b: base matrix at mats + mat_off[b] (k[b] x l[b], row-major), row
+ * multiplicities row_mult[row_off[b] .. row_off[b]+k[b]-1], column
+ * multiplicities col_mult[col_off[b] .. col_off[b]+l[b]-1].  Offsets count
+ * elements.  Multiplicities are >= 0; zero drops that row or column. */
+typedef struct {
+    int64_t batch;
+    const pq_c128* mats;
+    const int64_t* mat_off;
+    const int32_t* k;
+    const int32_t* l;
+    const int32_t* row_mult;
+    const int64_t* row_off;
+    const int32_t* col_mult;
+    const int64_t* col_off;
+} pq_batch;
+
+/* The same ragged layout with HOST pointers to the offsets, sizes and
+ * multiplicities only (no matrix values): what planning needs.  Same meaning
+ * as the fields of pq_batch. */
+typedef struct {
+    int64_t batch;
+    const int64_t* mat_off;
+    const int32_t* k;
+    const int32_t* l;
+    const int32_t* row_mult;
+    const int64_t* row_off;
+    const int32_t* col_mult;
+    const int64_t* col_off;
+} pq_batch_sizes;
+
+/* Execution method of a plan. */
+#define PQ_METHOD_BATCHED 0 /* one persistent launch for the whole batch (default)   */
+#define PQ_METHOD_PLAIN 1   /* one launch per permanent, issued back to back          */
+
+/* Plan options; zero-initialise and set what you need. */
+typedef struct {
+    int32_t method;          /* PQ_METHOD_*                                              */
+    int32_t use_graph;       /* 1: capture the batched launch in a CUDA graph and replay */
+    int32_t chunk_log2;      /* 0: per size class from the tuning table; else Gray-code
+                                chunk of about 2^chunk_log2 terms for every permanent     */
+    int32_t warps_per_block; /* 0: default (8)                                            */
+    int32_t blocks_per_sm;   /* 0: default (1)                                            */
+    int32_t reserved[3];
+} pq_plan_options;
+
+/* Opaque plan: the host-side schedule of one batch shape (which side of each
+ * permanent is summed, how its Gray-code range is cut into chunks, the order
+ * in which warps take them) plus the device workspace it needs.  Creating a
+ * plan is the only place the library allocates; executing it allocates
+ * nothing, reads no host memory and does not synchronise, so it can run
+ * inside stream capture.  A plan may be used by one stream at a time. */
+typedef struct pq_plan pq_plan;
+
+/* Plan a ragged permanent batch.  `sizes` is host memory and is copied; the
+ * matrix values are only read at execution.  opts may be NULL (defaults).
+ * Allocates device memory on the current device.
+ * Errors: PQ_ERR_ARG, PQ_ERR_UNSUPPORTED, PQ_ERR_NOMEM, PQ_ERR_CUDA. */
+int pq_plan_create(const pq_batch_sizes* sizes, const pq_plan_options* opts, pq_plan** out);
+
+/* Plan the boson-sampling batch of pq_bs_probs: m modes, input occupation
+ * input_occ[m] and output occupations output_occ[B*m] (row-major), both HOST
+ * memory and copied.  Every output pattern must hold as many photons as the
+ * input (PQ_ERR_ARG otherwise).  The plan also keeps the factorial
+ * normalisation 1/(prod t! prod s!) of every pattern. */
+int pq_plan_create_bs(int32_t m, const int32_t* input_occ, const int32_t* output_occ, int64_t B,
+                      const pq_plan_options* opts, pq_plan** out);
+
+/* Frees the plan and its device workspace (synchronises the device first). */
+int pq_plan_destroy(pq_plan* plan);
+
+/* Per(A_b) for every item of the batch (Eq. (per_def) with the multiplicities
+ * of Sec. 4.2), evaluated by the multiplicity-extended BB/FG formula over a
+ * mixed-radix Gray code in FP64 with double-double accumulation.
+ * b: device descriptor; out: device, batch entries.  plan: made by
+ * pq_plan_create for the same sizes, or NULL, in which case the call copies
+ * the sizes to the host, plans, runs the batched method and synchronises
+ * `stream` before returning (convenience path; it allocates). */
+int pq_permanent_batched(const pq_batch* b, pq_c128* out, pq_plan* plan, void* stream);
+
+/* Boson-sampling probabilities, Eq. (BS_prob).  U: device, m x m, U[out][in];
+ * input_occ: device, m; output_occ: device, B x m; probs: device, B doubles;
+ * amps: device, B complex, nullable -- receives per(U_{s,t}) (needed by the
+ * backward call).  plan: from pq_plan_create_bs for the same occupations, or
+ * NULL (the call then copies the occupations to the host, plans, runs and
+ * synchronises `stream`). */
+int pq_bs_probs(const pq_c128* U, int32_t m, const int32_t* input_occ,
+                const int32_t* output_occ, int64_t B, double* probs, pq_c128* amps,
+                pq_plan* plan, void* stream);
+
+/* Backward of pq_permanent_batched: grad_mats[b][i][j] = grad_out[b] *
+ * conj(d per(A_b) / d B_b[i][j]), where d per / d b_ij counts every one of the
+ * r_i c_j copies of b_ij (equal to r_i c_j per(B; r - e_i, c - e_j)).  Computed
+ * in the same Gray-code pass as the permanent, with prefix and suffix products
+ * of the column sums.  grad_out: device, batch; grad_mats: device, laid out
+ * like b->mats (entries of zero-multiplicity rows/columns are set to zero).
+ * plan: same rules as pq_permanent_batched. */
+int pq_permanent_backward(const pq_batch* b, const pq_c128* grad_out, pq_c128* grad_mats,
+                          pq_plan* plan, void* stream);
+
+/* Backward of pq_bs_probs for L with dL/dp_b = grad_probs[b]:
+ * grad_U (device, m x m) = sum_b 2 grad_probs[b] / (prod t! prod s!) *
+ * amps[b] * conj(d per(U_{s,t_b}) / dU), summed over patterns in a fixed
+ * order (no floating-point atomics, so the result is deterministic).
+ * amps: device, the amplitudes from the forward call.  grad_U is overwritten.
+ * plan: from pq_plan_create_bs for the same occupations, or NULL. */
+int pq_bs_probs_backward(const pq_c128* U, int32_t m, const int32_t* input_occ,
+                         const int32_t* output_occ, int64_t B, const double* grad_probs,
+                         const pq_c128* amps, pq_c128* grad_U, pq_plan* plan, void* stream);
+
+/* Clements mesh of m(m-1)/2 beamsplitters.  Beamsplitter k acts on modes
+ * (j_k, j_k + 1) with the 2 x 2 block [[t, -conj(r)], [r, t]], t = cos theta_k,
+ * r = exp(i phi_k) sin theta_k (Appendix A, "Beamsplitter gate").  Layout:
+ * m layers; layer q holds the pairs j = q mod 2, q mod 2 + 2, ... (j + 1 < m),
+ * numbered layer by layer with j ascending; U = T_{L-1} ... T_1 T_0.
+ * theta, phi: device, L doubles; U: device, m x m, written (U[out][in]).
+ * m <= PQ_MAX_DIM. */
+int pq_clements_forward(const double* theta, const double* phi, int32_t m, pq_c128* U,
+                        void* stream);
+
+/* Adjoint of pq_clements_forward: given grad_U (device, m x m, PyTorch
+ * convention) writes grad_theta and grad_phi (device, L doubles each).
+ * Uses the recurrence W <- T_k^H W T_k from W = grad_U U^H, so U (device, the
+ * forward output) is read rather than recomputed. */
+int pq_clements_backward(const double* theta, const double* phi, int32_t m, const pq_c128* U,
+                         const pq_c128* grad_U, double* grad_theta, double* grad_phi,
+                         void* stream);
+
+/* Times trial launches of the plan's batched kernel for each size class on
+ * the given data and stores the fastest chunk length per class in the plan
+ * (and in the process-wide tuning table used by later plans).  Synchronises
+ * `stream`.  b is the batch the plan was made for (device descriptor); for a
+ * boson-sampling plan pass b = NULL and U (device) instead. */
+int pq_autotune(pq_plan* plan, const pq_batch* b, const pq_c128* U, void* stream);
+
+/* Statistics of a plan, host memory: number of permanents, total Gray-code
+ * terms, algorithmic FP64 flops of one forward execution (FMA = 2), number of
+ * warp tasks and of kernel launches one execution makes. */
+typedef struct {
+    int64_t permanents;
+    int64_t terms;
+    double flops_forward;
+    double flops_backward;
+    int64_t tasks;
+    int64_t launches_forward;
+    int64_t launches_backward;
+    int32_t lmax;
+    int32_t reserved;
+} pq_plan_stats;
+int pq_plan_get_stats(const pq_plan* plan, pq_plan_stats* out);
+
+/* FP64 throughput probe: runs independent DFMA chains on every SM for about
+ * `iters` iterations and returns the measured rate in FLOP/s (FMA = 2) and
+ * the elapsed milliseconds.  Synchronises `stream`.  Measures the chip, not
+ * the paper's method; it provides the roofline denominator. */
+int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms, void* stream);
+
+/* ---- Diagnostics (host only; no GPU needed) ---------------------------- */
+
+/* How the planner treats one permanent: the side it sums, the digits of the
+ * mixed-radix Gray code (ascending radix; digit d belongs to summed row
+ * row_of_digit[d]) and how the code is cut into chunks. */
+typedef struct {
+    int32_t n, k, l;     /* photons; summed rows and product columns after orientation */
+    int32_t transposed;  /* 1 if the input's columns became the summed side         */
+    int32_t ndig, J;     /* Gray digits; low digits walked inside one chunk          */
+    int64_t terms;       /* Gray-code terms T = prod radix                            */
+    int64_t chunk_len;   /* L = prod of the J low radices                             */
+    int64_t chunks;      /* T / L                                                     */
+    int32_t radix[PQ_MAX_N];
+    int32_t row_of_digit[PQ_MAX_N];
+} pq_item_info;
+
+/* Plan one permanent of a k x l base with multiplicities row_mult[k],
+ * col_mult[l] (host memory) for the given chunk_log2 (0 = default) and
+ * describe it.  Errors as pq_plan_create. */
+int pq_plan_item_info(int32_t k, int32_t l, const int32_t* row_mult, const int32_t* col_mult,
+                      int32_t chunk_log2, pq_item_info* out);
+
+/* Run the kernels' warp-uniform Gray walk on the host: ndig <= 15 digits with
+ * radix[d] in [2, 15]; for `steps` steps writes the digit that changes and
+ * its direction (+1 / -1) to host arrays digit[steps], dir[steps]. */
+int pq_gray_walk(const int32_t* radix, int32_t ndig, int64_t steps, int32_t* digit, int32_t* dir);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* pq_last_error(void);
+
+/* Library version string. */
+const char* pq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PQ_GB300_H */

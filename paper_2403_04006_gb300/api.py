@@ -1,0 +1,255 @@
+"""Torch-facing API over the C ABI: device batches, plans and autograd
+Functions.  Tensors only carry device memory and streams; every step of the
+permanent path runs in the CUDA library (no CPU fallback)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import pq as _pq
+from .workloads import PermBatch
+
+
+def _stream_handle(stream: torch.cuda.Stream | None = None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _opts(method: str, use_graph: bool, chunk_log2: int, warps_per_block: int = 0,
+          blocks_per_sm: int = 0) -> _pq.pq_plan_options:
+    o = _pq.pq_plan_options()
+    o.method = {"batched": _pq.PQ_METHOD_BATCHED, "plain": _pq.PQ_METHOD_PLAIN}[method]
+    o.use_graph = 1 if use_graph else 0
+    o.chunk_log2 = int(chunk_log2)
+    o.warps_per_block = int(warps_per_block)
+    o.blocks_per_sm = int(blocks_per_sm)
+    return o
+
+
+class DeviceBatch:
+    """A ragged batch of base matrices resident on the GPU, plus the host
+    copy of its sizes that planning needs."""
+
+    def __init__(self, pb: PermBatch, device: str | torch.device = "cuda",
+                 mats: torch.Tensor | None = None):
+        self.host = pb
+        dev = torch.device(device)
+        self.mats = (mats if mats is not None
+                     else torch.from_numpy(pb.mats).to(dev))
+        self.mat_off = torch.from_numpy(pb.mat_off).to(dev)
+        self.k = torch.from_numpy(pb.k).to(dev)
+        self.l = torch.from_numpy(pb.l).to(dev)
+        self.row_mult = torch.from_numpy(pb.row_mult).to(dev)
+        self.row_off = torch.from_numpy(pb.row_off).to(dev)
+        self.col_mult = torch.from_numpy(pb.col_mult).to(dev)
+        self.col_off = torch.from_numpy(pb.col_off).to(dev)
+
+    @property
+    def batch(self) -> int:
+        return self.host.batch
+
+    def c_struct(self, mats: torch.Tensor | None = None) -> _pq.pq_batch:
+        m = self.mats if mats is None else mats
+        b = _pq.pq_batch()
+        b.batch = self.batch
+        b.mats = _ptr(m) if m.numel() else None
+        for f in ("mat_off", "k", "l", "row_mult", "row_off", "col_mult", "col_off"):
+            t = getattr(self, f)
+            setattr(b, f, _ptr(t) if t.numel() else None)
+        return b
+
+    def sizes_struct(self):
+        h = self.host
+        keep = [np.ascontiguousarray(x) for x in
+                (h.mat_off, h.k, h.l, h.row_mult, h.row_off, h.col_mult, h.col_off)]
+        s = _pq.pq_batch_sizes()
+        s.batch = h.batch
+        s.mat_off, s.k, s.l, s.row_mult, s.row_off, s.col_mult, s.col_off = [
+            x.ctypes.data if x.size else None for x in keep]
+        return s, keep
+
+
+class Plan:
+    """Owns a pq_plan (host schedule + device workspace)."""
+
+    def __init__(self, handle: int, kind: str):
+        self.handle = handle
+        self.kind = kind
+
+    @classmethod
+    def for_batch(cls, pb: PermBatch | DeviceBatch, method: str = "batched",
+                  use_graph: bool = False, chunk_log2: int = 0, warps_per_block: int = 0,
+                  blocks_per_sm: int = 0) -> "Plan":
+        db = pb if isinstance(pb, DeviceBatch) else None
+        host = db.host if db is not None else pb
+        keep = [np.ascontiguousarray(x) for x in
+                (host.mat_off, host.k, host.l, host.row_mult, host.row_off, host.col_mult,
+                 host.col_off)]
+        s = _pq.pq_batch_sizes()
+        s.batch = host.batch
+        s.mat_off, s.k, s.l, s.row_mult, s.row_off, s.col_mult, s.col_off = [
+            x.ctypes.data if x.size else None for x in keep]
+        h = _pq.pq_plan_create(s, _opts(method, use_graph, chunk_log2, warps_per_block,
+                                        blocks_per_sm))
+        return cls(h, "batch")
+
+    @classmethod
+    def for_bs(cls, m: int, s, t, method: str = "batched", use_graph: bool = False,
+               chunk_log2: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0) -> "Plan":
+        s = np.ascontiguousarray(np.asarray(s, dtype=np.int32))
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.int32).reshape(-1, m))
+        h = _pq.pq_plan_create_bs(int(m), s, t, int(t.shape[0]),
+                                  _opts(method, use_graph, chunk_log2, warps_per_block,
+                                        blocks_per_sm))
+        return cls(h, "bs")
+
+    def stats(self) -> dict:
+        st = _pq.pq_plan_get_stats(self.handle)
+        return {f: getattr(st, f) for f, _ in _pq.pq_plan_stats._fields_ if f != "reserved"}
+
+    def autotune(self, db: DeviceBatch | None = None, U: torch.Tensor | None = None,
+                 stream=None):
+        b = db.c_struct() if db is not None else None
+        _pq.pq_autotune(self.handle, b, _ptr(U), _stream_handle(stream))
+
+    def close(self):
+        if self.handle:
+            _pq.pq_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# functional API
+# --------------------------------------------------------------------------
+def permanent_batched(db: DeviceBatch, plan: Plan | None = None, out: torch.Tensor | None = None,
+                      mats: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    dev = db.mats.device
+    if out is None:
+        out = torch.empty(db.batch, dtype=torch.complex128, device=dev)
+    _pq.pq_permanent_batched(db.c_struct(mats), _ptr(out) if db.batch else None,
+                             plan.handle if plan else None, _stream_handle(stream))
+    return out
+
+
+def permanent_backward(db: DeviceBatch, grad_out: torch.Tensor, plan: Plan | None = None,
+                       mats: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    m = db.mats if mats is None else mats
+    grad = torch.empty_like(m)
+    _pq.pq_permanent_backward(db.c_struct(mats), _ptr(grad_out.contiguous()), _ptr(grad),
+                              plan.handle if plan else None, _stream_handle(stream))
+    return grad
+
+
+def bs_probs(U: torch.Tensor, s: torch.Tensor, t: torch.Tensor, plan: Plan | None = None,
+             want_amps: bool = True, stream=None):
+    m = U.shape[0]
+    B = t.shape[0]
+    probs = torch.empty(B, dtype=torch.float64, device=U.device)
+    amps = torch.empty(B, dtype=torch.complex128, device=U.device) if want_amps else None
+    _pq.pq_bs_probs(_ptr(U), m, _ptr(s), _ptr(t), B, _ptr(probs), _ptr(amps),
+                    plan.handle if plan else None, _stream_handle(stream))
+    return probs, amps
+
+
+def bs_probs_backward(U, s, t, grad_probs, amps, plan: Plan | None = None, stream=None):
+    m = U.shape[0]
+    gU = torch.empty_like(U)
+    _pq.pq_bs_probs_backward(_ptr(U), m, _ptr(s), _ptr(t), t.shape[0],
+                             _ptr(grad_probs.contiguous()), _ptr(amps), _ptr(gU),
+                             plan.handle if plan else None, _stream_handle(stream))
+    return gU
+
+
+def clements_forward(theta: torch.Tensor, phi: torch.Tensor, m: int, stream=None):
+    U = torch.empty((m, m), dtype=torch.complex128, device=theta.device)
+    _pq.pq_clements_forward(_ptr(theta), _ptr(phi), m, _ptr(U), _stream_handle(stream))
+    return U
+
+
+def clements_backward(theta, phi, m, U, grad_U, stream=None):
+    gt = torch.empty_like(theta)
+    gp = torch.empty_like(phi)
+    _pq.pq_clements_backward(_ptr(theta), _ptr(phi), m, _ptr(U), _ptr(grad_U.contiguous()),
+                             _ptr(gt), _ptr(gp), _stream_handle(stream))
+    return gt, gp
+
+
+# --------------------------------------------------------------------------
+# autograd
+# --------------------------------------------------------------------------
+class Permanent(torch.autograd.Function):
+    """per of every item of a ragged batch; ``mats`` is the packed complex128
+    matrix tensor of the batch (differentiable)."""
+
+    @staticmethod
+    def forward(ctx, mats, db: DeviceBatch, plan: Plan | None):
+        mats = mats.contiguous()
+        ctx.db, ctx.plan = db, plan
+        ctx.save_for_backward(mats)
+        return permanent_batched(db, plan, mats=mats)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (mats,) = ctx.saved_tensors
+        g = permanent_backward(ctx.db, grad_out.to(torch.complex128), ctx.plan, mats=mats)
+        return g, None, None
+
+
+class BSProbs(torch.autograd.Function):
+    """Boson-sampling probabilities p(s, t_b) of Eq. (BS_prob) as a function of U."""
+
+    @staticmethod
+    def forward(ctx, U, s, t, plan: Plan | None):
+        U = U.contiguous()
+        probs, amps = bs_probs(U, s, t, plan)
+        ctx.plan = plan
+        ctx.save_for_backward(U, s, t, amps)
+        return probs
+
+    @staticmethod
+    def backward(ctx, grad_probs):
+        U, s, t, amps = ctx.saved_tensors
+        gU = bs_probs_backward(U, s, t, grad_probs.to(torch.float64), amps, ctx.plan)
+        return gU, None, None, None
+
+
+class ClementsMesh(torch.autograd.Function):
+    """U(theta, phi) of the Clements beamsplitter mesh."""
+
+    @staticmethod
+    def forward(ctx, theta, phi, m: int):
+        theta = theta.contiguous()
+        phi = phi.contiguous()
+        U = clements_forward(theta, phi, m)
+        ctx.m = m
+        ctx.save_for_backward(theta, phi, U)
+        return U
+
+    @staticmethod
+    def backward(ctx, grad_U):
+        theta, phi, U = ctx.saved_tensors
+        gt, gp = clements_backward(theta, phi, ctx.m, U, grad_U.to(torch.complex128))
+        return gt, gp, None
+
+
+def probe_fp64_peak(iters: int = 1 << 16, stream=None) -> tuple[float, float]:
+    """Measured FP64 rate of this GPU (FLOP/s, FMA = 2) and the probe's ms."""
+    return _pq.pq_probe_fp64_peak(iters, _stream_handle(stream))

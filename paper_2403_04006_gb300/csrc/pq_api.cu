@@ -1,0 +1,1189 @@
+// pq_api.cu -- the C ABI (include/pq.h): argument checks, planning, launches.
+//
+// Planning (host): for every permanent, drop zero-multiplicity rows/columns,
+// pick the side whose Gray code has fewer terms ("column or row
+// multiplicities", Sec. 4.2), fix one copy of the least repeated row, order
+// the digits by radix, cut the code into chunks of the low digits and the
+// chunks into warp tasks.  Execution (device) then needs no host reads and no
+// allocation, so it can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pq.h"
+#include "pq_kernels.h"
+#include "pq_plan.h"
+
+using namespace pqi;
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define PQ_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(PQ_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+extern "C" const char* pq_last_error(void) { return g_err.c_str(); }
+extern "C" const char* pq_version(void) { return "pq-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------- tuning table
+// Process-wide chunk length (log2) per (product-column class, photon number),
+// filled by pq_autotune and read by later plans.
+static std::mutex g_tune_mu;
+static int g_tune[5][PQ_MAX_N + 1];
+static bool g_tune_init = false;
+
+static int tune_get(int lclass, int n)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune_init) {
+        for (auto& row : g_tune)
+            for (int& v : row)
+                v = 0;
+        g_tune_init = true;
+    }
+    int ci = 0;
+    while (ci < 5 && kLmaxClasses[ci] != lclass)
+        ++ci;
+    if (ci == 5 || n < 0 || n > PQ_MAX_N)
+        return 0;
+    return g_tune[ci][n];
+}
+
+static void tune_set(int lclass, int n, int v)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int ci = 0;
+    while (ci < 5 && kLmaxClasses[ci] != lclass)
+        ++ci;
+    if (ci == 5 || n < 0 || n > PQ_MAX_N)
+        return;
+    g_tune[ci][n] = v;
+}
+
+// ---------------------------------------------------------------- planning
+static const int64_t kMaxTerms = int64_t(1) << 62;
+
+// Terms of the Gray code when the given side is summed: the least repeated
+// line keeps one copy fixed (radix m_f = mult_f), every other line has radix
+// mult + 1.  Returns -1 on overflow.
+static int64_t side_terms(const std::vector<int32_t>& mult)
+{
+    if (mult.empty())
+        return 1;
+    size_t f = std::min_element(mult.begin(), mult.end()) - mult.begin();
+    int64_t T = 1;
+    for (size_t i = 0; i < mult.size(); ++i) {
+        int64_t rad = (i == f) ? mult[i] : mult[i] + 1;
+        if (rad <= 0)
+            rad = 1;
+        if (T > kMaxTerms / rad)
+            return -1;
+        T *= rad;
+    }
+    return T;
+}
+
+// Build the oriented item for base (k0 x l0) with multiplicities r, c whose
+// element (i, j) sits at src_off + i * ld0 + j.
+static int build_item(const int32_t* r, const int32_t* c, int k0, int l0, int64_t src_off,
+                      int64_t ld0, ItemPlan& it)
+{
+    if (k0 < 0 || l0 < 0 || k0 > PQ_MAX_DIM || l0 > PQ_MAX_DIM)
+        return fail(k0 < 0 || l0 < 0 ? PQ_ERR_ARG : PQ_ERR_UNSUPPORTED,
+                    "base matrix %d x %d outside [0, %d]", k0, l0, PQ_MAX_DIM);
+    std::vector<int32_t> rs, cs, rm, cm;
+    int nr = 0, nc = 0;
+    for (int i = 0; i < k0; ++i) {
+        if (r[i] < 0)
+            return fail(PQ_ERR_ARG, "negative row multiplicity");
+        if (r[i] > 0) {
+            rs.push_back(i);
+            rm.push_back(r[i]);
+            nr += r[i];
+        }
+    }
+    for (int j = 0; j < l0; ++j) {
+        if (c[j] < 0)
+            return fail(PQ_ERR_ARG, "negative column multiplicity");
+        if (c[j] > 0) {
+            cs.push_back(j);
+            cm.push_back(c[j]);
+            nc += c[j];
+        }
+    }
+    if (nr != nc)
+        return fail(PQ_ERR_ARG, "sum of row multiplicities (%d) != sum of column multiplicities (%d)",
+                    nr, nc);
+    if (nr > PQ_MAX_N)
+        return fail(PQ_ERR_UNSUPPORTED, "n = %d above PQ_MAX_N = %d", nr, PQ_MAX_N);
+    it = ItemPlan();
+    it.n = nr;
+    it.src_off = src_off;
+    if (nr == 0) {
+        it.trivial = true;
+        it.T = 0;
+        return PQ_OK;
+    }
+    int64_t Tr = side_terms(rm), Tc = side_terms(cm);
+    if (Tr < 0 && Tc < 0)
+        return fail(PQ_ERR_UNSUPPORTED, "term count above 2^62");
+    bool transpose = (Tr < 0) || (Tc >= 0 && Tc < Tr);
+    if (transpose) {
+        it.transposed = true;
+        it.ridx = cs;
+        it.rmul = cm;
+        it.cidx = rs;
+        it.cmul = rm;
+        it.si = 1;
+        it.sj = (int32_t)ld0;
+        it.T = Tc;
+    } else {
+        it.ridx = rs;
+        it.rmul = rm;
+        it.cidx = cs;
+        it.cmul = cm;
+        it.si = (int32_t)ld0;
+        it.sj = 1;
+        it.T = Tr;
+    }
+    it.k = (int32_t)it.ridx.size();
+    it.l = (int32_t)it.cidx.size();
+    if (it.l > PQ_MAX_PRODUCT_COLS)
+        return fail(PQ_ERR_UNSUPPORTED, "%d product-side columns above %d", it.l,
+                    PQ_MAX_PRODUCT_COLS);
+    // digits: fixed copy on the least repeated row, ascending radix
+    int f = (int)(std::min_element(it.rmul.begin(), it.rmul.end()) - it.rmul.begin());
+    struct Dg {
+        int rad, row, top;
+    };
+    std::vector<Dg> dg;
+    for (int i = 0; i < it.k; ++i) {
+        if (i == f) {
+            if (it.rmul[i] >= 2)
+                dg.push_back({it.rmul[i], i, it.rmul[i] - 1});
+        } else {
+            dg.push_back({it.rmul[i] + 1, i, it.rmul[i]});
+        }
+    }
+    std::stable_sort(dg.begin(), dg.end(), [](const Dg& a, const Dg& b) { return a.rad < b.rad; });
+    for (const Dg& d : dg) {
+        it.drow.push_back(d.row);
+        it.drad.push_back(d.rad);
+        it.dtop.push_back(d.top);
+    }
+    return PQ_OK;
+}
+
+// Cut the item's code into chunks of the lowest digits: the longest prefix of
+// digits whose radix product stays within the target length.
+static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits)
+{
+    if (it.trivial) {
+        it.J = 0;
+        it.L = 1;
+        it.nchunks = 0;
+        return;
+    }
+    int64_t target = it.T / kWarp;  // aim for at least one full warp of chunks
+    int64_t cap = int64_t(1) << std::max(0, std::min(log2_cap, 30));
+    if (target > cap)
+        target = cap;
+    if (target < 1)
+        target = 1;
+    int J = 0;
+    int64_t L = 1;
+    while (J < (int)it.drad.size() && J < jmax && it.drad[J] <= kMaxLowRadix &&
+           L * it.drad[J] <= target) {
+        L *= it.drad[J];
+        ++J;
+    }
+    it.J = J;
+    it.L = L;
+    it.nchunks = it.T / L;
+    it.weighted = false;
+    for (int d = 0; d < J; ++d)
+        if (it.drad[d] > 2)
+            it.weighted = true;
+}
+
+static double fwd_flops_per_term(const ItemPlan& it)
+{
+    // column update 2l, n-1 complex products at 6, accumulate 2, weight 2
+    return 2.0 * it.l + 6.0 * (it.n - 1) + 2.0 + (it.weighted ? 2.0 : 0.0);
+}
+
+static double bwd_flops_per_term(const ItemPlan& it)
+{
+    return fwd_flops_per_term(it) + 18.0 * it.l + 8.0 * it.k * it.l;
+}
+
+static int default_log2_for(const pq_plan* P, const ItemPlan& it)
+{
+    if (P->opts.chunk_log2 > 0)
+        return P->opts.chunk_log2;
+    if (it.n >= 0 && it.n < (int)P->class_log2.size() && P->class_log2[it.n] > 0)
+        return P->class_log2[it.n];
+    int tuned = tune_get(P->lmax, it.n);
+    if (tuned > 0)
+        return tuned;
+    return 10;
+}
+
+template <typename T>
+static int dev_upload(T** dst, const std::vector<T>& src)
+{
+    if (*dst) {
+        cudaFree(*dst);
+        *dst = nullptr;
+    }
+    size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e != cudaSuccess)
+        return fail(PQ_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    if (!src.empty()) {
+        e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return fail(PQ_ERR_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));
+    }
+    return PQ_OK;
+}
+
+static void free_plan_device(pq_plan* P)
+{
+    void* ptrs[] = {P->desc_d,        P->meta_d,           P->tasks_batched_d, P->tasks_plain_d,
+                    P->partials_d,    P->counters_d,       P->err_d,           P->gpart_d,
+                    P->gpart_off_d,   P->grad_local_d,     P->grad_local_off_d, P->item_mat_off_d,
+                    P->item_k_d,      P->item_l_d,         P->grad_out_tmp_d};
+    for (void* p : ptrs)
+        if (p)
+            cudaFree(p);
+    void* bptrs[] = {P->desc_bwd_d, P->tasks_bwd_plain_d, P->tasks_bwd_batched_d};
+    for (void* p : bptrs)
+        if (p)
+            cudaFree(p);
+    P->desc_bwd_d = nullptr;
+    P->tasks_bwd_plain_d = P->tasks_bwd_batched_d = nullptr;
+    P->bwd_ready = false;
+    P->desc_d = nullptr;
+    P->meta_d = nullptr;
+    P->tasks_batched_d = P->tasks_plain_d = nullptr;
+    P->partials_d = nullptr;
+    P->counters_d = P->err_d = nullptr;
+    P->gpart_d = nullptr;
+    P->gpart_off_d = nullptr;
+    P->grad_local_d = nullptr;
+    P->grad_local_off_d = nullptr;
+    P->item_mat_off_d = nullptr;
+    P->item_k_d = P->item_l_d = nullptr;
+    P->grad_out_tmp_d = nullptr;
+    if (P->graph) {
+        cudaGraphExecDestroy(P->graph);
+        P->graph = nullptr;
+    }
+}
+
+// Chunks, tasks, descriptors, device upload.
+static int schedule_and_upload(pq_plan* P)
+{
+    const int64_t np = (int64_t)P->items.size();
+    P->nperm = np;
+    int lmax_needed = 1, kmax = 1;
+    for (const ItemPlan& it : P->items) {
+        lmax_needed = std::max(lmax_needed, it.l);
+        kmax = std::max(kmax, it.k);
+    }
+    P->lmax = lmax_class(lmax_needed);
+    if (P->lmax < 0)
+        return fail(PQ_ERR_UNSUPPORTED, "product side of %d columns", lmax_needed);
+    P->kmax = kmax;
+    for (ItemPlan& it : P->items)
+        choose_chunks(it, default_log2_for(P, it));
+
+    P->desc_h.assign(np, PermDesc{});
+    P->meta_h.clear();
+    P->tasks_plain_h.clear();
+    P->plain_first.assign(np + 1, 0);
+    std::vector<double> task_cost;
+    int32_t slot = 0;
+    double flops_f = 0.0, flops_b = 0.0;
+    int64_t terms = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        ItemPlan& it = P->items[p];
+        PermDesc& D = P->desc_h[p];
+        D.T = it.T;
+        D.nchunks = it.nchunks;
+        D.src_off = it.src_off;
+        D.k = it.k;
+        D.l = it.l;
+        D.n = it.n;
+        D.si = it.si;
+        D.sj = it.sj;
+        D.meta = (int32_t)P->meta_h.size();
+        D.ndig = (int32_t)it.drow.size();
+        D.J = it.J;
+        D.weighted = it.weighted ? 1 : 0;
+        D.out = (int32_t)p;
+        D.trivial = it.trivial ? 1 : 0;
+        D.L = it.L;
+        D.norm = it.norm;
+        auto app = [&](const std::vector<int32_t>& v) {
+            P->meta_h.insert(P->meta_h.end(), v.begin(), v.end());
+        };
+        app(it.ridx);
+        app(it.cidx);
+        app(it.rmul);
+        app(it.cmul);
+        app(it.drow);
+        app(it.drad);
+        app(it.dtop);
+        int64_t nt = it.trivial ? 1 : (it.nchunks + kWarp - 1) / kWarp;
+        if (nt > (int64_t(1) << 30))
+            return fail(PQ_ERR_UNSUPPORTED, "too many tasks for one permanent");
+        D.ntasks = (int32_t)nt;
+        D.slot0 = slot;
+        slot += (int32_t)nt;
+        P->plain_first[p] = (int64_t)P->tasks_plain_h.size();
+        const double fpt = it.trivial ? 0.0 : fwd_flops_per_term(it);
+        const double init = 2.0 * (it.drow.size() - it.J) * it.l + 2.0 * it.l;
+        for (int64_t q = 0; q < nt; ++q) {
+            Task t;
+            t.perm = (int32_t)p;
+            t.part = (int32_t)q;
+            P->tasks_plain_h.push_back(t);
+            task_cost.push_back((double)it.L * fpt + init);
+        }
+        if (!it.trivial) {
+            terms += it.T;
+            flops_f += (double)it.T * fpt;
+            flops_b += (double)it.T * bwd_flops_per_term(it);
+        }
+        if (slot < 0)
+            return fail(PQ_ERR_UNSUPPORTED, "too many tasks");
+    }
+    P->plain_first[np] = (int64_t)P->tasks_plain_h.size();
+    // batched order: longest task first (LPT), ties by permanent then part
+    std::vector<int64_t> order(P->tasks_plain_h.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return task_cost[a] > task_cost[b]; });
+    P->tasks_batched_h.resize(order.size());
+    for (size_t q = 0; q < order.size(); ++q)
+        P->tasks_batched_h[q] = P->tasks_plain_h[order[q]];
+
+    // launch geometry
+    int wpb = P->opts.warps_per_block > 0 ? P->opts.warps_per_block : 8;
+    const int per_warp = fwd_smem_per_warp(P->kmax, P->lmax);
+    while (wpb > 1 && wpb * per_warp > 200 * 1024)
+        --wpb;
+    if (per_warp > 200 * 1024)
+        return fail(PQ_ERR_UNSUPPORTED, "shared memory per warp %d too large", per_warp);
+    P->wpb = wpb;
+    int bps = P->opts.blocks_per_sm > 0 ? P->opts.blocks_per_sm : 1;
+    P->blocks = std::max(1, P->num_sms * bps);
+
+    P->stats.permanents = np;
+    P->stats.terms = terms;
+    P->stats.flops_forward = flops_f;
+    P->stats.flops_backward = flops_b;
+    P->stats.tasks = (int64_t)P->tasks_plain_h.size();
+    P->stats.launches_forward = (P->opts.method == PQ_METHOD_PLAIN) ? np : 1;
+    P->stats.launches_backward = (P->opts.method == PQ_METHOD_PLAIN) ? np + 1 : 2;
+    P->stats.lmax = P->lmax;
+
+    // upload
+    int rc;
+    if ((rc = dev_upload(&P->desc_d, P->desc_h)) != PQ_OK)
+        return rc;
+    if ((rc = dev_upload(&P->meta_d, P->meta_h)) != PQ_OK)
+        return rc;
+    if ((rc = dev_upload(&P->tasks_plain_d, P->tasks_plain_h)) != PQ_OK)
+        return rc;
+    if ((rc = dev_upload(&P->tasks_batched_d, P->tasks_batched_h)) != PQ_OK)
+        return rc;
+    if (P->partials_d)
+        cudaFree(P->partials_d);
+    P->partials_d = nullptr;
+    PQ_CUDA(cudaMalloc((void**)&P->partials_d, std::max<size_t>(slot, 1) * 4 * sizeof(double)));
+    if (P->counters_d)
+        cudaFree(P->counters_d);
+    P->counters_d = nullptr;
+    PQ_CUDA(cudaMalloc((void**)&P->counters_d, (size_t)(np + 1) * sizeof(int32_t)));
+    if (!P->err_d) {
+        PQ_CUDA(cudaMalloc((void**)&P->err_d, sizeof(int32_t)));
+        PQ_CUDA(cudaMemset(P->err_d, 0, sizeof(int32_t)));
+    }
+    cudaError_t e = fwd_prepare(P->lmax, P->wpb * per_warp);
+    if (e != cudaSuccess)
+        return fail(PQ_ERR_CUDA, "kernel attribute setup failed: %s", cudaGetErrorString(e));
+    if (P->graph) {
+        cudaGraphExecDestroy(P->graph);
+        P->graph = nullptr;
+    }
+    return PQ_OK;
+}
+
+static int plan_common_init(pq_plan* P, const pq_plan_options* opts)
+{
+    if (opts)
+        P->opts = *opts;
+    if (P->opts.method != PQ_METHOD_BATCHED && P->opts.method != PQ_METHOD_PLAIN)
+        return fail(PQ_ERR_ARG, "unknown method %d", P->opts.method);
+    if (P->opts.chunk_log2 < 0 || P->opts.chunk_log2 > 30)
+        return fail(PQ_ERR_ARG, "chunk_log2 %d outside [0, 30]", P->opts.chunk_log2);
+    if (P->opts.warps_per_block < 0 || P->opts.warps_per_block > 16)
+        return fail(PQ_ERR_ARG, "warps_per_block %d outside [0, 16]", P->opts.warps_per_block);
+    if (P->opts.blocks_per_sm < 0 || P->opts.blocks_per_sm > 32)
+        return fail(PQ_ERR_ARG, "blocks_per_sm %d outside [0, 32]", P->opts.blocks_per_sm);
+    PQ_CUDA(cudaGetDevice(&P->device));
+    PQ_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+    return PQ_OK;
+}
+
+extern "C" int pq_plan_create(const pq_batch_sizes* sz, const pq_plan_options* opts,
+                              pq_plan** out)
+{
+    if (!sz || !out)
+        return fail(PQ_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (sz->batch < 0)
+        return fail(PQ_ERR_ARG, "negative batch");
+    if (sz->batch > 0 && (!sz->mat_off || !sz->k || !sz->l || !sz->row_mult || !sz->row_off ||
+                          !sz->col_mult || !sz->col_off))
+        return fail(PQ_ERR_ARG, "null size array");
+    if (sz->batch > (int64_t(1) << 30))
+        return fail(PQ_ERR_UNSUPPORTED, "batch above 2^30");
+    pq_plan* P = new (std::nothrow) pq_plan();
+    if (!P)
+        return fail(PQ_ERR_NOMEM, "host allocation failed");
+    int rc = plan_common_init(P, opts);
+    if (rc != PQ_OK) {
+        delete P;
+        return rc;
+    }
+    P->kind = 0;
+    P->items.resize(sz->batch);
+    P->item_mat_off.resize(sz->batch);
+    P->item_k.resize(sz->batch);
+    P->item_l.resize(sz->batch);
+    int64_t off = 0;
+    for (int64_t b = 0; b < sz->batch; ++b) {
+        if (sz->row_off[b] < 0 || sz->col_off[b] < 0 || sz->mat_off[b] < 0) {
+            delete P;
+            return fail(PQ_ERR_ARG, "negative offset at item %lld", (long long)b);
+        }
+        rc = build_item(sz->row_mult + sz->row_off[b], sz->col_mult + sz->col_off[b], sz->k[b],
+                        sz->l[b], sz->mat_off[b], sz->l[b], P->items[b]);
+        if (rc != PQ_OK) {
+            delete P;
+            return fail(rc, "item %lld: %s", (long long)b, g_err.c_str());
+        }
+        P->item_mat_off[b] = sz->mat_off[b];
+        P->item_k[b] = sz->k[b];
+        P->item_l[b] = sz->l[b];
+        off += (int64_t)sz->k[b] * sz->l[b];
+    }
+    P->total_mat_elems = off;
+    P->class_log2.assign(PQ_MAX_N + 1, 0);
+    rc = schedule_and_upload(P);
+    if (rc != PQ_OK) {
+        free_plan_device(P);
+        delete P;
+        return rc;
+    }
+    *out = P;
+    return PQ_OK;
+}
+
+static double factorial_d(int n)
+{
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i)
+        r *= (double)i;
+    return r;
+}
+
+extern "C" int pq_plan_create_bs(int32_t m, const int32_t* in_occ, const int32_t* out_occ,
+                                 int64_t B, const pq_plan_options* opts, pq_plan** out)
+{
+    if (!out || !in_occ || (B > 0 && !out_occ))
+        return fail(PQ_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (m <= 0 || m > PQ_MAX_DIM)
+        return fail(m <= 0 ? PQ_ERR_ARG : PQ_ERR_UNSUPPORTED, "m = %d outside [1, %d]", m,
+                    PQ_MAX_DIM);
+    if (B < 0)
+        return fail(PQ_ERR_ARG, "negative pattern count");
+    if (B > (int64_t(1) << 30))
+        return fail(PQ_ERR_UNSUPPORTED, "more than 2^30 patterns");
+    int ns = 0;
+    double fs = 1.0;
+    for (int i = 0; i < m; ++i) {
+        if (in_occ[i] < 0)
+            return fail(PQ_ERR_ARG, "negative input occupation");
+        ns += in_occ[i];
+        fs *= factorial_d(in_occ[i]);
+    }
+    pq_plan* P = new (std::nothrow) pq_plan();
+    if (!P)
+        return fail(PQ_ERR_NOMEM, "host allocation failed");
+    int rc = plan_common_init(P, opts);
+    if (rc != PQ_OK) {
+        delete P;
+        return rc;
+    }
+    P->kind = 1;
+    P->m = m;
+    P->in_occ.assign(in_occ, in_occ + m);
+    P->out_occ.assign(out_occ, out_occ + B * m);
+    P->items.resize(B);
+    for (int64_t b = 0; b < B; ++b) {
+        const int32_t* t = out_occ + b * m;
+        int nt = 0;
+        double ft = 1.0;
+        for (int i = 0; i < m; ++i) {
+            if (t[i] < 0) {
+                delete P;
+                return fail(PQ_ERR_ARG, "negative output occupation in pattern %lld",
+                            (long long)b);
+            }
+            nt += t[i];
+            ft *= factorial_d(t[i]);
+        }
+        if (nt != ns) {
+            delete P;
+            return fail(PQ_ERR_ARG, "pattern %lld has %d photons, input has %d", (long long)b, nt,
+                        ns);
+        }
+        // rows = output modes (t), columns = input modes (s); U[out][in]
+        rc = build_item(t, in_occ, m, m, 0, m, P->items[b]);
+        if (rc != PQ_OK) {
+            delete P;
+            return fail(rc, "pattern %lld: %s", (long long)b, g_err.c_str());
+        }
+        P->items[b].norm = 1.0 / (ft * fs);
+    }
+    P->class_log2.assign(PQ_MAX_N + 1, 0);
+    rc = schedule_and_upload(P);
+    if (rc != PQ_OK) {
+        free_plan_device(P);
+        delete P;
+        return rc;
+    }
+    *out = P;
+    return PQ_OK;
+}
+
+extern "C" int pq_plan_destroy(pq_plan* P)
+{
+    if (!P)
+        return PQ_OK;
+    cudaDeviceSynchronize();
+    free_plan_device(P);
+    delete P;
+    return PQ_OK;
+}
+
+extern "C" int pq_plan_get_stats(const pq_plan* P, pq_plan_stats* out)
+{
+    if (!P || !out)
+        return fail(PQ_ERR_ARG, "null argument");
+    *out = P->stats;
+    return PQ_OK;
+}
+
+// ---------------------------------------------------------------- execution
+static ExecArgs exec_args(pq_plan* P, const void* src, void* amps, double* probs, bool batched)
+{
+    ExecArgs a;
+    a.desc = P->desc_d;
+    a.meta = P->meta_d;
+    a.tasks = batched ? P->tasks_batched_d : P->tasks_plain_d;
+    a.ntasks = (int64_t)P->tasks_plain_h.size();
+    a.src = reinterpret_cast<const double2*>(src);
+    a.out_amp = reinterpret_cast<double2*>(amps);
+    a.out_prob = probs;
+    a.partials = P->partials_d;
+    a.counters = P->counters_d;
+    a.err = P->err_d;
+    return a;
+}
+
+static int run_forward_raw(pq_plan* P, const void* src, void* amps, double* probs,
+                           cudaStream_t st)
+{
+    PQ_CUDA(cudaMemsetAsync(P->counters_d, 0, (size_t)(P->nperm + 1) * sizeof(int32_t), st));
+    if (P->nperm == 0)
+        return PQ_OK;
+    if (P->opts.method == PQ_METHOD_PLAIN) {
+        ExecArgs a = exec_args(P, src, amps, probs, false);
+        for (int64_t p = 0; p < P->nperm; ++p) {
+            cudaError_t e = fwd_launch_plain(P->lmax, a, P->plain_first[p], P->plain_first[p + 1],
+                                             P->kmax, P->wpb, st);
+            if (e != cudaSuccess)
+                return fail(PQ_ERR_CUDA, "plain launch failed: %s", cudaGetErrorString(e));
+        }
+        return PQ_OK;
+    }
+    ExecArgs a = exec_args(P, src, amps, probs, true);
+    cudaError_t e = fwd_launch_persistent(P->lmax, a, P->kmax, P->blocks, P->wpb, st);
+    if (e != cudaSuccess)
+        return fail(PQ_ERR_CUDA, "persistent launch failed: %s", cudaGetErrorString(e));
+    return PQ_OK;
+}
+
+static int run_forward(pq_plan* P, const void* src, void* amps, double* probs, cudaStream_t st)
+{
+    const bool graph = P->opts.use_graph && P->opts.method == PQ_METHOD_BATCHED && st != nullptr;
+    if (!graph)
+        return run_forward_raw(P, src, amps, probs, st);
+    const void* key[4] = {src, amps, probs, st};
+    if (P->graph && std::memcmp(key, P->graph_key, sizeof(key)) != 0) {
+        cudaGraphExecDestroy(P->graph);
+        P->graph = nullptr;
+    }
+    if (!P->graph) {
+        cudaGraph_t g = nullptr;
+        PQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = run_forward_raw(P, src, amps, probs, st);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc != PQ_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess)
+            return fail(PQ_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&P->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            P->graph = nullptr;
+            return fail(PQ_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        }
+        std::memcpy(P->graph_key, key, sizeof(key));
+    }
+    PQ_CUDA(cudaGraphLaunch(P->graph, st));
+    return PQ_OK;
+}
+
+// Sizes of a device batch descriptor copied to the host (convenience path).
+struct HostSizes {
+    std::vector<int32_t> k, l, rm, cm;
+    std::vector<int64_t> ro, co, mo;
+    pq_batch_sizes view() const
+    {
+        pq_batch_sizes s;
+        s.batch = (int64_t)k.size();
+        s.mat_off = mo.data();
+        s.k = k.data();
+        s.l = l.data();
+        s.row_mult = rm.data();
+        s.row_off = ro.data();
+        s.col_mult = cm.data();
+        s.col_off = co.data();
+        return s;
+    }
+};
+
+static int fetch_sizes(const pq_batch* b, HostSizes& h)
+{
+    const int64_t n = b->batch;
+    h.k.resize(n);
+    h.l.resize(n);
+    h.ro.resize(n);
+    h.co.resize(n);
+    h.mo.resize(n);
+    if (n == 0)
+        return PQ_OK;
+    if (!b->k || !b->l || !b->row_off || !b->col_off || !b->row_mult || !b->col_mult ||
+        !b->mat_off)
+        return fail(PQ_ERR_ARG, "null pointer in batch descriptor");
+    PQ_CUDA(cudaMemcpy(h.k.data(), b->k, n * 4, cudaMemcpyDeviceToHost));
+    PQ_CUDA(cudaMemcpy(h.l.data(), b->l, n * 4, cudaMemcpyDeviceToHost));
+    PQ_CUDA(cudaMemcpy(h.ro.data(), b->row_off, n * 8, cudaMemcpyDeviceToHost));
+    PQ_CUDA(cudaMemcpy(h.co.data(), b->col_off, n * 8, cudaMemcpyDeviceToHost));
+    PQ_CUDA(cudaMemcpy(h.mo.data(), b->mat_off, n * 8, cudaMemcpyDeviceToHost));
+    int64_t nr = 0, nc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (h.k[i] < 0 || h.l[i] < 0 || h.ro[i] < 0 || h.co[i] < 0)
+            return fail(PQ_ERR_ARG, "negative size or offset at item %lld", (long long)i);
+        nr = std::max(nr, h.ro[i] + h.k[i]);
+        nc = std::max(nc, h.co[i] + h.l[i]);
+    }
+    h.rm.resize(nr);
+    h.cm.resize(nc);
+    if (nr)
+        PQ_CUDA(cudaMemcpy(h.rm.data(), b->row_mult, nr * 4, cudaMemcpyDeviceToHost));
+    if (nc)
+        PQ_CUDA(cudaMemcpy(h.cm.data(), b->col_mult, nc * 4, cudaMemcpyDeviceToHost));
+    return PQ_OK;
+}
+
+static int check_batch_plan(const pq_plan* P, const pq_batch* b)
+{
+    if (P->kind != 0)
+        return fail(PQ_ERR_STATE, "plan was made for boson sampling, not a permanent batch");
+    if (b->batch != P->nperm)
+        return fail(PQ_ERR_STATE, "plan made for %lld items, batch has %lld",
+                    (long long)P->nperm, (long long)b->batch);
+    return PQ_OK;
+}
+
+extern "C" int pq_permanent_batched(const pq_batch* b, pq_c128* out, pq_plan* plan, void* stream)
+{
+    if (!b || (b->batch > 0 && (!out || !b->mats)))
+        return fail(PQ_ERR_ARG, "null argument");
+    if (b->batch < 0)
+        return fail(PQ_ERR_ARG, "negative batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan) {
+        int rc = check_batch_plan(plan, b);
+        if (rc != PQ_OK)
+            return rc;
+        return run_forward(plan, b->mats, out, nullptr, st);
+    }
+    HostSizes h;
+    int rc = fetch_sizes(b, h);
+    if (rc != PQ_OK)
+        return rc;
+    pq_batch_sizes sz = h.view();
+    pq_plan* P = nullptr;
+    rc = pq_plan_create(&sz, nullptr, &P);
+    if (rc != PQ_OK)
+        return rc;
+    rc = run_forward_raw(P, b->mats, out, nullptr, st);
+    if (rc == PQ_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess)
+            rc = fail(PQ_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
+    }
+    pq_plan_destroy(P);
+    return rc;
+}
+
+extern "C" int pq_bs_probs(const pq_c128* U, int32_t m, const int32_t* in_occ,
+                           const int32_t* out_occ, int64_t B, double* probs, pq_c128* amps,
+                           pq_plan* plan, void* stream)
+{
+    if (!U || !in_occ || (B > 0 && (!out_occ || !probs)))
+        return fail(PQ_ERR_ARG, "null argument");
+    if (m <= 0 || m > PQ_MAX_DIM || B < 0)
+        return fail(PQ_ERR_ARG, "bad sizes m = %d, B = %lld", m, (long long)B);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan) {
+        if (plan->kind != 1 || plan->m != m || plan->nperm != B)
+            return fail(PQ_ERR_STATE, "plan was made for different occupations");
+        return run_forward(plan, U, amps, probs, st);
+    }
+    std::vector<int32_t> s(m), t((size_t)B * m);
+    PQ_CUDA(cudaMemcpy(s.data(), in_occ, m * 4, cudaMemcpyDeviceToHost));
+    if (B)
+        PQ_CUDA(cudaMemcpy(t.data(), out_occ, (size_t)B * m * 4, cudaMemcpyDeviceToHost));
+    pq_plan* P = nullptr;
+    int rc = pq_plan_create_bs(m, s.data(), t.data(), B, nullptr, &P);
+    if (rc != PQ_OK)
+        return rc;
+    rc = run_forward_raw(P, U, amps, probs, st);
+    if (rc == PQ_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess)
+            rc = fail(PQ_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
+    }
+    pq_plan_destroy(P);
+    return rc;
+}
+
+// ---------------------------------------------------------------- probe
+extern "C" int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms, void* stream)
+{
+    if (!flops_per_s || !ms || iters <= 0)
+        return fail(PQ_ERR_ARG, "bad argument");
+    cudaError_t e = fp64_probe(iters, flops_per_s, ms, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return fail(PQ_ERR_CUDA, "fp64 probe failed: %s", cudaGetErrorString(e));
+    return PQ_OK;
+}
+
+// ---------------------------------------------------------------- backward
+// The backward pass keeps per-lane running sums for the low digits in shared
+// memory, so it uses its own, shorter chunks (at most kBwdMaxLowDigits low
+// digits, about 2^5 terms).
+static int ensure_backward(pq_plan* P)
+{
+    if (P->bwd_ready)
+        return PQ_OK;
+    const int64_t np = P->nperm;
+    std::vector<ItemPlan> items = P->items;
+    P->desc_bwd_h = P->desc_h;
+    P->tasks_bwd_plain_h.clear();
+    P->plain_first_bwd.assign(np + 1, 0);
+    std::vector<double> cost;
+    std::vector<int64_t> gpart_off(np), gl_off(np);
+    int64_t gpart = 0, gl = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        ItemPlan& it = items[p];
+        choose_chunks(it, 5, kBwdMaxLowDigits);
+        PermDesc& D = P->desc_bwd_h[p];
+        D.J = it.J;
+        D.L = it.L;
+        D.nchunks = it.nchunks;
+        D.weighted = it.weighted ? 1 : 0;
+        const int64_t nt = it.trivial ? 1 : (it.nchunks + kWarp - 1) / kWarp;
+        D.ntasks = (int32_t)nt;
+        D.slot0 = 0;
+        P->plain_first_bwd[p] = (int64_t)P->tasks_bwd_plain_h.size();
+        const int64_t kl = (int64_t)it.k * it.l;
+        gpart_off[p] = gpart;
+        gl_off[p] = gl;
+        gpart += nt * kl;
+        gl += kl;
+        const double fpt = it.trivial ? 0.0 : bwd_flops_per_term(it);
+        for (int64_t q = 0; q < nt; ++q) {
+            Task t;
+            t.perm = (int32_t)p;
+            t.part = (int32_t)q;
+            P->tasks_bwd_plain_h.push_back(t);
+            cost.push_back((double)it.L * fpt + 4.0 * kl);
+        }
+    }
+    P->plain_first_bwd[np] = (int64_t)P->tasks_bwd_plain_h.size();
+    std::vector<int64_t> order(P->tasks_bwd_plain_h.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    P->tasks_bwd_batched_h.resize(order.size());
+    for (size_t q = 0; q < order.size(); ++q)
+        P->tasks_bwd_batched_h[q] = P->tasks_bwd_plain_h[order[q]];
+
+    int rc;
+    if ((rc = dev_upload(&P->desc_bwd_d, P->desc_bwd_h)) != PQ_OK)
+        return rc;
+    if ((rc = dev_upload(&P->tasks_bwd_plain_d, P->tasks_bwd_plain_h)) != PQ_OK)
+        return rc;
+    if ((rc = dev_upload(&P->tasks_bwd_batched_d, P->tasks_bwd_batched_h)) != PQ_OK)
+        return rc;
+    if ((rc = dev_upload(&P->gpart_off_d, gpart_off)) != PQ_OK)
+        return rc;
+    if ((rc = dev_upload(&P->grad_local_off_d, gl_off)) != PQ_OK)
+        return rc;
+    PQ_CUDA(cudaMalloc((void**)&P->gpart_d, std::max<int64_t>(gpart, 1) * 2 * sizeof(double)));
+    PQ_CUDA(cudaMalloc((void**)&P->grad_local_d, std::max<int64_t>(gl, 1) * sizeof(double2)));
+    P->gpart_elems = (size_t)gpart;
+    P->grad_local_elems = (size_t)gl;
+    if (P->kind == 0) {
+        if ((rc = dev_upload(&P->item_mat_off_d, P->item_mat_off)) != PQ_OK)
+            return rc;
+        if ((rc = dev_upload(&P->item_k_d, P->item_k)) != PQ_OK)
+            return rc;
+        if ((rc = dev_upload(&P->item_l_d, P->item_l)) != PQ_OK)
+            return rc;
+    }
+    int wpb = 4;
+    const int per_warp = bwd_smem_bytes_for(P->kmax, P->lmax, kBwdMaxLowDigits);
+    while (wpb > 1 && wpb * per_warp > 200 * 1024)
+        --wpb;
+    if (per_warp > 200 * 1024)
+        return fail(PQ_ERR_UNSUPPORTED, "backward shared memory per warp %d too large", per_warp);
+    P->bwd_wpb = wpb;
+    cudaError_t e = bwd_prepare(P->lmax, wpb * per_warp);
+    if (e != cudaSuccess)
+        return fail(PQ_ERR_CUDA, "backward attribute setup failed: %s", cudaGetErrorString(e));
+    P->bwd_ready = true;
+    return PQ_OK;
+}
+
+static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, const double* grad_prob,
+                        const pq_c128* amps, cudaStream_t st)
+{
+    int rc = ensure_backward(P);
+    if (rc != PQ_OK)
+        return rc;
+    PQ_CUDA(cudaMemsetAsync(P->counters_d, 0, (size_t)(P->nperm + 1) * sizeof(int32_t), st));
+    if (P->nperm == 0)
+        return PQ_OK;
+    BwdArgs a;
+    a.desc = P->desc_bwd_d;
+    a.meta = P->meta_d;
+    a.ntasks = (int64_t)P->tasks_bwd_plain_h.size();
+    a.src = reinterpret_cast<const double2*>(src);
+    a.grad_out = reinterpret_cast<const double2*>(grad_out);
+    a.amps = reinterpret_cast<const double2*>(amps);
+    a.grad_prob = grad_prob;
+    a.gpart = P->gpart_d;
+    a.gpart_off = P->gpart_off_d;
+    a.grad_local = P->grad_local_d;
+    a.grad_local_off = P->grad_local_off_d;
+    a.counters = P->counters_d;
+    a.err = P->err_d;
+    cudaError_t e;
+    if (P->opts.method == PQ_METHOD_PLAIN) {
+        a.tasks = P->tasks_bwd_plain_d;
+        for (int64_t p = 0; p < P->nperm; ++p) {
+            e = bwd_launch_plain(P->lmax, a, P->plain_first_bwd[p], P->plain_first_bwd[p + 1],
+                                 P->kmax, P->bwd_wpb, st);
+            if (e != cudaSuccess)
+                return fail(PQ_ERR_CUDA, "plain backward launch failed: %s", cudaGetErrorString(e));
+        }
+    } else {
+        a.tasks = P->tasks_bwd_batched_d;
+        e = bwd_launch_persistent(P->lmax, a, P->kmax, P->blocks, P->bwd_wpb, st);
+        if (e != cudaSuccess)
+            return fail(PQ_ERR_CUDA, "backward launch failed: %s", cudaGetErrorString(e));
+    }
+    return PQ_OK;
+}
+
+extern "C" int pq_permanent_backward(const pq_batch* b, const pq_c128* grad_out, pq_c128* grad_mats,
+                                     pq_plan* plan, void* stream)
+{
+    if (!b || (b->batch > 0 && (!grad_out || !grad_mats || !b->mats)))
+        return fail(PQ_ERR_ARG, "null argument");
+    if (b->batch < 0)
+        return fail(PQ_ERR_ARG, "negative batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    pq_plan* P = plan;
+    HostSizes h;
+    if (!P) {
+        int rc = fetch_sizes(b, h);
+        if (rc != PQ_OK)
+            return rc;
+        pq_batch_sizes sz = h.view();
+        rc = pq_plan_create(&sz, nullptr, &P);
+        if (rc != PQ_OK)
+            return rc;
+    } else {
+        int rc = check_batch_plan(P, b);
+        if (rc != PQ_OK)
+            return rc;
+    }
+    int rc = run_backward(P, b->mats, grad_out, nullptr, nullptr, st);
+    if (rc == PQ_OK && P->nperm > 0) {
+        cudaError_t e = scatter_grad_batch(P->desc_bwd_d, P->meta_d, P->nperm, P->grad_local_d,
+                                           P->grad_local_off_d, P->item_mat_off_d, P->item_l_d,
+                                           P->item_k_d, reinterpret_cast<double2*>(grad_mats),
+                                           P->total_mat_elems, st);
+        if (e != cudaSuccess)
+            rc = fail(PQ_ERR_CUDA, "gradient scatter failed: %s", cudaGetErrorString(e));
+    }
+    if (!plan) {
+        if (rc == PQ_OK) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess)
+                rc = fail(PQ_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
+        }
+        pq_plan_destroy(P);
+    }
+    return rc;
+}
+
+extern "C" int pq_bs_probs_backward(const pq_c128* U, int32_t m, const int32_t* in_occ,
+                                    const int32_t* out_occ, int64_t B, const double* grad_probs,
+                                    const pq_c128* amps, pq_c128* grad_U, pq_plan* plan,
+                                    void* stream)
+{
+    if (!U || !in_occ || !grad_U || (B > 0 && (!out_occ || !grad_probs || !amps)))
+        return fail(PQ_ERR_ARG, "null argument");
+    if (m <= 0 || m > PQ_MAX_DIM || B < 0)
+        return fail(PQ_ERR_ARG, "bad sizes m = %d, B = %lld", m, (long long)B);
+    cudaStream_t st = (cudaStream_t)stream;
+    pq_plan* P = plan;
+    if (!P) {
+        std::vector<int32_t> s(m), t((size_t)B * m);
+        PQ_CUDA(cudaMemcpy(s.data(), in_occ, m * 4, cudaMemcpyDeviceToHost));
+        if (B)
+            PQ_CUDA(cudaMemcpy(t.data(), out_occ, (size_t)B * m * 4, cudaMemcpyDeviceToHost));
+        int rc = pq_plan_create_bs(m, s.data(), t.data(), B, nullptr, &P);
+        if (rc != PQ_OK)
+            return rc;
+    } else if (P->kind != 1 || P->m != m || P->nperm != B) {
+        return fail(PQ_ERR_STATE, "plan was made for different occupations");
+    }
+    int rc = run_backward(P, U, nullptr, grad_probs, amps, st);
+    if (rc == PQ_OK) {
+        cudaError_t e = scatter_grad_bs(P->desc_bwd_d, P->meta_d, P->nperm, m, P->grad_local_d,
+                                        P->grad_local_off_d, reinterpret_cast<double2*>(grad_U),
+                                        st);
+        if (e != cudaSuccess)
+            rc = fail(PQ_ERR_CUDA, "gradient scatter failed: %s", cudaGetErrorString(e));
+    }
+    if (!plan) {
+        if (rc == PQ_OK) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess)
+                rc = fail(PQ_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
+        }
+        pq_plan_destroy(P);
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------- Clements mesh
+extern "C" int pq_clements_forward(const double* theta, const double* phi, int32_t m, pq_c128* U,
+                                   void* stream)
+{
+    if (!theta || !phi || !U)
+        return fail(PQ_ERR_ARG, "null argument");
+    if (m < 1 || m > PQ_MAX_DIM)
+        return fail(m < 1 ? PQ_ERR_ARG : PQ_ERR_UNSUPPORTED, "m = %d outside [1, %d]", m,
+                    PQ_MAX_DIM);
+    cudaError_t e = clements_forward(theta, phi, m, reinterpret_cast<double2*>(U),
+                                     (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return fail(PQ_ERR_CUDA, "clements forward failed: %s", cudaGetErrorString(e));
+    return PQ_OK;
+}
+
+extern "C" int pq_clements_backward(const double* theta, const double* phi, int32_t m,
+                                    const pq_c128* U, const pq_c128* grad_U, double* grad_theta,
+                                    double* grad_phi, void* stream)
+{
+    if (!theta || !phi || !U || !grad_U || !grad_theta || !grad_phi)
+        return fail(PQ_ERR_ARG, "null argument");
+    if (m < 1 || m > PQ_MAX_DIM)
+        return fail(m < 1 ? PQ_ERR_ARG : PQ_ERR_UNSUPPORTED, "m = %d outside [1, %d]", m,
+                    PQ_MAX_DIM);
+    cudaError_t e = clements_backward(theta, phi, m, reinterpret_cast<const double2*>(U),
+                                      reinterpret_cast<const double2*>(grad_U), grad_theta,
+                                      grad_phi, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return fail(PQ_ERR_CUDA, "clements backward failed: %s", cudaGetErrorString(e));
+    return PQ_OK;
+}
+
+// ---------------------------------------------------------------- autotuning
+// For every photon number present, try chunk lengths 2^4 .. 2^12 (one class at
+// a time, the others fixed) on the plan's own data and keep the fastest.
+extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void* stream)
+{
+    if (!P)
+        return fail(PQ_ERR_ARG, "null plan");
+    const void* src = nullptr;
+    if (P->kind == 0) {
+        if (!b)
+            return fail(PQ_ERR_ARG, "permanent plan needs the batch descriptor");
+        int rc = check_batch_plan(P, b);
+        if (rc != PQ_OK)
+            return rc;
+        src = b->mats;
+    } else {
+        if (!U)
+            return fail(PQ_ERR_ARG, "boson-sampling plan needs U");
+        src = U;
+    }
+    if (P->nperm == 0)
+        return PQ_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    double2* amps = nullptr;
+    PQ_CUDA(cudaMalloc((void**)&amps, (size_t)P->nperm * sizeof(double2)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int> present(PQ_MAX_N + 1, 0);
+    for (const ItemPlan& it : P->items)
+        if (!it.trivial)
+            present[it.n] = 1;
+    const int saved_opt = P->opts.chunk_log2;
+    P->opts.chunk_log2 = 0;
+    const int cands[] = {4, 6, 8, 10, 12};
+    int rc = PQ_OK;
+    auto time_once = [&](float& ms) -> int {
+        int r = schedule_and_upload(P);
+        if (r != PQ_OK)
+            return r;
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            r = run_forward_raw(P, src, amps, nullptr, st);
+            if (r != PQ_OK)
+                return r;
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess)
+                return fail(PQ_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, t);
+        }
+        ms = best;
+        return PQ_OK;
+    };
+    for (int n = 0; n <= PQ_MAX_N && rc == PQ_OK; ++n) {
+        if (!present[n])
+            continue;
+        int best_c = 10;
+        float best_t = 1e30f;
+        for (int cnd : cands) {
+            P->class_log2[n] = cnd;
+            float t = 0.0f;
+            rc = time_once(t);
+            if (rc != PQ_OK)
+                break;
+            if (t < best_t * 0.98f) {
+                best_t = t;
+                best_c = cnd;
+            }
+        }
+        P->class_log2[n] = best_c;
+        tune_set(P->lmax, n, best_c);
+    }
+    P->opts.chunk_log2 = saved_opt;
+    if (rc == PQ_OK)
+        rc = schedule_and_upload(P);
+    P->bwd_ready = false;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(amps);
+    return rc;
+}
+
+// ---------------------------------------------------------------- diagnostics
+extern "C" int pq_plan_item_info(int32_t k, int32_t l, const int32_t* row_mult,
+                                 const int32_t* col_mult, int32_t chunk_log2, pq_item_info* out)
+{
+    if (!out || (k > 0 && !row_mult) || (l > 0 && !col_mult))
+        return fail(PQ_ERR_ARG, "null argument");
+    if (chunk_log2 < 0 || chunk_log2 > 30)
+        return fail(PQ_ERR_ARG, "chunk_log2 outside [0, 30]");
+    ItemPlan it;
+    int rc = build_item(row_mult, col_mult, k, l, 0, l, it);
+    if (rc != PQ_OK)
+        return rc;
+    choose_chunks(it, chunk_log2 > 0 ? chunk_log2 : 10);
+    std::memset(out, 0, sizeof(*out));
+    out->n = it.n;
+    out->k = it.k;
+    out->l = it.l;
+    out->transposed = it.transposed ? 1 : 0;
+    out->ndig = (int32_t)it.drow.size();
+    out->J = it.J;
+    out->terms = it.T;
+    out->chunk_len = it.L;
+    out->chunks = it.nchunks;
+    for (size_t d = 0; d < it.drow.size() && d < (size_t)PQ_MAX_N; ++d) {
+        out->radix[d] = it.drad[d];
+        out->row_of_digit[d] = it.drow[d];
+    }
+    return PQ_OK;
+}

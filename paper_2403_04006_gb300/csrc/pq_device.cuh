@@ -1,0 +1,200 @@
+// pq_device.cuh -- device helpers shared by the forward and backward kernels:
+// double-double accumulation, complex FP64 products, warp reductions, the
+// warp-uniform mixed-radix Gray walk and the per-task shared-memory staging.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pq_internal.h"
+
+namespace pqi {
+
+// ---------------------------------------------------------------- dd numbers
+struct dd2 {  // complex double-double: (hi, lo) for the real and imaginary parts
+    double rh, rl, ih, il;
+};
+
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
+{
+    s = __dadd_rn(a, b);
+    double bv = __dsub_rn(s, a);
+    double av = __dsub_rn(s, bv);
+    e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+}
+
+__device__ __forceinline__ void fast_two_sum(double a, double b, double& s, double& e)
+{
+    s = __dadd_rn(a, b);
+    e = __dsub_rn(b, __dsub_rn(s, a));
+}
+
+// hi + lo += x (compensated; lo collects the exact rounding errors)
+__device__ __forceinline__ void dd_acc(double& hi, double& lo, double x)
+{
+    double s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo = __dadd_rn(lo, e);
+}
+
+// (ah, al) + (bh, bl), renormalised
+__device__ __forceinline__ void dd_add(double& ah, double& al, double bh, double bl)
+{
+    double s, e, t, f;
+    two_sum(ah, bh, s, e);
+    two_sum(al, bl, t, f);
+    e = __dadd_rn(e, t);
+    fast_two_sum(s, e, s, e);
+    e = __dadd_rn(e, f);
+    fast_two_sum(s, e, ah, al);
+}
+
+__device__ __forceinline__ void dd2_add(dd2& a, const dd2& b)
+{
+    dd_add(a.rh, a.rl, b.rh, b.rl);
+    dd_add(a.ih, a.il, b.ih, b.il);
+}
+
+// (h, l) * w for a double w
+__device__ __forceinline__ void dd_mul_d(double& h, double& l, double w)
+{
+    double p = __dmul_rn(h, w);
+    double e = __fma_rn(h, w, -p);
+    e = __fma_rn(l, w, e);
+    fast_two_sum(p, e, h, l);
+}
+
+__device__ __forceinline__ dd2 shfl_down_dd2(const dd2& v, int off)
+{
+    dd2 r;
+    r.rh = __shfl_down_sync(0xffffffffu, v.rh, off);
+    r.rl = __shfl_down_sync(0xffffffffu, v.rl, off);
+    r.ih = __shfl_down_sync(0xffffffffu, v.ih, off);
+    r.il = __shfl_down_sync(0xffffffffu, v.il, off);
+    return r;
+}
+
+// Tree sum over the 32 lanes in a fixed order; lane 0 holds the result.
+__device__ __forceinline__ dd2 warp_sum_dd2(dd2 v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        dd2 o = shfl_down_dd2(v, off);
+        dd2_add(v, o);
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- complex FP64
+// p * s with two DMUL and two DFMA
+__device__ __forceinline__ double2 cmul(double2 p, double2 s)
+{
+    double2 r;
+    r.x = __fma_rn(p.x, s.x, -__dmul_rn(p.y, s.y));
+    r.y = __fma_rn(p.x, s.y, __dmul_rn(p.y, s.x));
+    return r;
+}
+
+// acc += p * s (NEG: acc -= p * s) with four DFMA and no separate product
+template <bool NEG>
+__device__ __forceinline__ void cfma_acc(double2& acc, double2 p, double2 s)
+{
+    if (NEG) {
+        acc.x = __fma_rn(-p.x, s.x, acc.x);
+        acc.x = __fma_rn(p.y, s.y, acc.x);
+        acc.y = __fma_rn(-p.x, s.y, acc.y);
+        acc.y = __fma_rn(-p.y, s.x, acc.y);
+    } else {
+        acc.x = __fma_rn(p.x, s.x, acc.x);
+        acc.x = __fma_rn(-p.y, s.y, acc.x);
+        acc.y = __fma_rn(p.x, s.y, acc.y);
+        acc.y = __fma_rn(p.y, s.x, acc.y);
+    }
+}
+
+// ---------------------------------------------------------------- binomials
+// Exact C(top, g) for the small tops of low digits (top <= 14).
+__host__ __device__ __forceinline__ uint64_t binom_u64(int top, int g)
+{
+    uint64_t r = 1;
+    for (int i = 1; i <= g; ++i)
+        r = r * (uint64_t)(top - g + i) / (uint64_t)i;
+    return r;
+}
+
+// C(top, g) in double (exact while it stays below 2^53).
+__device__ __forceinline__ double binom_f64(int top, int g)
+{
+    double r = 1.0;
+    for (int i = 1; i <= g; ++i)
+        r = r * (double)(top - g + i) / (double)i;
+    return r;
+}
+
+// ---------------------------------------------------------------- metadata views
+struct MetaView {
+    const int32_t* ridx;
+    const int32_t* cidx;
+    const int32_t* rmul;
+    const int32_t* cmul;
+    const int32_t* drow;
+    const int32_t* drad;
+    const int32_t* dtop;
+};
+
+__device__ __forceinline__ MetaView meta_view(const int32_t* pool, const PermDesc& D)
+{
+    MetaView m;
+    m.ridx = pool + D.meta;
+    m.cidx = m.ridx + D.k;
+    m.rmul = m.cidx + D.l;
+    m.cmul = m.rmul + D.k;
+    m.drow = m.cmul + D.l;
+    m.drad = m.drow + D.ndig;
+    m.dtop = m.drad + D.ndig;
+    return m;
+}
+
+// Warp-uniform state of the walk over the J low digits of a chunk.  Digit d
+// occupies bits [4d, 4d+4) of v (odometer value) and g (Gray value).
+struct LowWalk {
+    uint64_t v, g;      // packed digits
+    uint32_t dir;       // bit d set: digit d currently moves down
+    uint64_t radm1;     // packed radix - 1 of each low digit
+    uint64_t topp;      // packed binomial tops of the low digits
+};
+
+// Advance one Gray step; returns the changed digit and sets up = +1/-1.
+__host__ __device__ __forceinline__ int low_step(LowWalk& w, int& up)
+{
+    int d = 0;
+    while (((w.v >> (4 * d)) & 15u) == ((w.radm1 >> (4 * d)) & 15u)) {
+        w.v &= ~(uint64_t(15) << (4 * d));
+        w.dir ^= (1u << d);
+        ++d;
+    }
+    w.v += uint64_t(1) << (4 * d);
+    if ((w.dir >> d) & 1u) {
+        up = -1;
+        w.g -= uint64_t(1) << (4 * d);
+    } else {
+        up = 1;
+        w.g += uint64_t(1) << (4 * d);
+    }
+    return d;
+}
+
+// prod_{d<J} C(top_d, g_d) for the current low Gray value
+__host__ __device__ __forceinline__ uint64_t low_weight(const LowWalk& w, int J)
+{
+    uint64_t r = 1;
+    for (int d = 0; d < J; ++d) {
+        int g = int((w.g >> (4 * d)) & 15u);
+        int top = int((w.topp >> (4 * d)) & 15u);
+        if (g)
+            r *= binom_u64(top, g);
+    }
+    return r;
+}
+
+}  // namespace pqi

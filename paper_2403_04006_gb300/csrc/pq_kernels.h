@@ -1,0 +1,73 @@
+// pq_kernels.h -- host-side entry points of the kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pq_internal.h"
+
+namespace pqi {
+
+// Product-side column bound classes the kernels are compiled for.
+constexpr int kLmaxClasses[] = {8, 16, 24, 32, 40};
+
+inline int lmax_class(int l)
+{
+    for (int c : kLmaxClasses)
+        if (l <= c)
+            return c;
+    return -1;
+}
+
+// ---- forward (glynn_fwd.cu)
+int fwd_smem_per_warp(int kmax, int lmax);
+cudaError_t fwd_prepare(int lmax, int smem_bytes);
+cudaError_t fwd_launch_persistent(int lmax, const ExecArgs& a, int kmax, int blocks, int wpb,
+                                  cudaStream_t st);
+cudaError_t fwd_launch_plain(int lmax, const ExecArgs& a, int64_t t_begin, int64_t t_end,
+                             int kmax, int wpb, cudaStream_t st);
+
+// ---- backward (glynn_bwd.cu)
+struct BwdArgs {
+    const PermDesc* desc;
+    const int32_t* meta;
+    const Task* tasks;
+    int64_t ntasks;
+    const double2* src;
+    const double2* grad_out;   // per permanent: dL/dper (PyTorch convention), nullable
+    const double2* amps;       // boson sampling: per values, used with grad_prob
+    const double* grad_prob;   // boson sampling: dL/dp, nullable
+    double* gpart;             // per task slot: k*l complex (oriented), 2 doubles each
+    int64_t* gpart_off;        // per permanent: offset (in complex entries) of slot 0
+    double2* grad_local;       // per permanent: oriented k x l gradient (complex)
+    int64_t* grad_local_off;   // per permanent: offset of its block
+    int32_t* counters;
+    int32_t* err;
+};
+int bwd_smem_per_warp(int kmax, int lmax);
+int bwd_smem_bytes_for(int kmax, int lmax, int jb);
+constexpr int kBwdMaxLowDigits = 6;  // low digits the backward workspace holds
+cudaError_t bwd_prepare(int lmax, int smem_bytes);
+cudaError_t bwd_launch_persistent(int lmax, const BwdArgs& a, int kmax, int blocks, int wpb,
+                                  cudaStream_t st);
+cudaError_t bwd_launch_plain(int lmax, const BwdArgs& a, int64_t t_begin, int64_t t_end,
+                             int kmax, int wpb, cudaStream_t st);
+
+// Scatter of oriented per-permanent gradients into the caller's layouts.
+cudaError_t scatter_grad_batch(const PermDesc* desc, const int32_t* meta, int64_t nperm,
+                               const double2* grad_local, const int64_t* grad_local_off,
+                               const int64_t* item_mat_off, const int32_t* item_l,
+                               const int32_t* item_k, double2* grad_mats, int64_t total_elems,
+                               cudaStream_t st);
+cudaError_t scatter_grad_bs(const PermDesc* desc, const int32_t* meta, int64_t nperm, int32_t m,
+                            const double2* grad_local, const int64_t* grad_local_off,
+                            double2* grad_U, cudaStream_t st);
+
+// ---- Clements mesh (clements.cu)
+cudaError_t clements_forward(const double* theta, const double* phi, int m, double2* U,
+                             cudaStream_t st);
+cudaError_t clements_backward(const double* theta, const double* phi, int m, const double2* U,
+                              const double2* gU, double* gtheta, double* gphi, cudaStream_t st);
+
+// ---- FP64 probe (fp64_probe.cu)
+cudaError_t fp64_probe(int64_t iters, double* flops_per_s, double* ms, cudaStream_t st);
+
+}  // namespace pqi

@@ -1,0 +1,195 @@
+"""Thin Python binding of the C ABI in include/pq.h.
+
+Every ``pq_*`` function here has the name of the C entry point it calls and
+only marshals arguments (torch tensors to device pointers, numpy arrays to
+host pointers); all arithmetic of the permanent path runs in the CUDA
+library.  The library must have been built (``paper_2403_04006_gb300.build``);
+if it is missing every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpq_gb300.so")
+
+PQ_OK = 0
+PQ_ERR_ARG = -1
+PQ_ERR_UNSUPPORTED = -2
+PQ_ERR_CUDA = -3
+PQ_ERR_TIMEOUT = -4
+PQ_ERR_NOMEM = -5
+PQ_ERR_STATE = -6
+PQ_METHOD_BATCHED = 0
+PQ_METHOD_PLAIN = 1
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+
+class pq_batch(ctypes.Structure):
+    _fields_ = [("batch", _i64), ("mats", _vp), ("mat_off", _vp), ("k", _vp), ("l", _vp),
+                ("row_mult", _vp), ("row_off", _vp), ("col_mult", _vp), ("col_off", _vp)]
+
+
+class pq_batch_sizes(ctypes.Structure):
+    _fields_ = [("batch", _i64), ("mat_off", _vp), ("k", _vp), ("l", _vp), ("row_mult", _vp),
+                ("row_off", _vp), ("col_mult", _vp), ("col_off", _vp)]
+
+
+class pq_plan_options(ctypes.Structure):
+    _fields_ = [("method", _i32), ("use_graph", _i32), ("chunk_log2", _i32),
+                ("warps_per_block", _i32), ("blocks_per_sm", _i32), ("reserved", _i32 * 3)]
+
+
+class pq_plan_stats(ctypes.Structure):
+    _fields_ = [("permanents", _i64), ("terms", _i64), ("flops_forward", ctypes.c_double),
+                ("flops_backward", ctypes.c_double), ("tasks", _i64),
+                ("launches_forward", _i64), ("launches_backward", _i64), ("lmax", _i32),
+                ("reserved", _i32)]
+
+
+# name -> (restype, argtypes)
+_SIGNATURES = {
+    "pq_plan_create": (_i32, [ctypes.POINTER(pq_batch_sizes), ctypes.POINTER(pq_plan_options),
+                              ctypes.POINTER(_vp)]),
+    "pq_plan_create_bs": (_i32, [_i32, _vp, _vp, _i64, ctypes.POINTER(pq_plan_options),
+                                 ctypes.POINTER(_vp)]),
+    "pq_plan_destroy": (_i32, [_vp]),
+    "pq_permanent_batched": (_i32, [ctypes.POINTER(pq_batch), _vp, _vp, _vp]),
+    "pq_bs_probs": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "pq_permanent_backward": (_i32, [ctypes.POINTER(pq_batch), _vp, _vp, _vp, _vp]),
+    "pq_bs_probs_backward": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "pq_clements_forward": (_i32, [_vp, _vp, _i32, _vp, _vp]),
+    "pq_clements_backward": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "pq_autotune": (_i32, [_vp, ctypes.POINTER(pq_batch), _vp, _vp]),
+    "pq_plan_get_stats": (_i32, [_vp, ctypes.POINTER(pq_plan_stats)]),
+    "pq_probe_fp64_peak": (_i32, [_i64, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), _vp]),
+    "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
+    "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
+    "pq_last_error": (ctypes.c_char_p, []),
+    "pq_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing "
+                               "(run paper_2403_04006_gb300.build.build())")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class PQError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} returned {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, where: str):
+    if rc != PQ_OK:
+        msg = load_library().pq_last_error().decode(errors="replace")
+        raise PQError(rc, where, msg)
+
+
+# --------------------------------------------------------------------------
+# raw entry points (same names as the C ABI)
+# --------------------------------------------------------------------------
+def pq_plan_create(sizes: pq_batch_sizes, opts: pq_plan_options | None = None) -> int:
+    out = _vp()
+    _check(load_library().pq_plan_create(ctypes.byref(sizes),
+                                         ctypes.byref(opts) if opts else None,
+                                         ctypes.byref(out)), "pq_plan_create")
+    return out.value
+
+
+def pq_plan_create_bs(m: int, input_occ: np.ndarray, output_occ: np.ndarray, B: int,
+                      opts: pq_plan_options | None = None) -> int:
+    out = _vp()
+    _check(load_library().pq_plan_create_bs(m, input_occ.ctypes.data, output_occ.ctypes.data, B,
+                                            ctypes.byref(opts) if opts else None,
+                                            ctypes.byref(out)), "pq_plan_create_bs")
+    return out.value
+
+
+def pq_plan_destroy(plan: int):
+    _check(load_library().pq_plan_destroy(plan), "pq_plan_destroy")
+
+
+def pq_permanent_batched(b: pq_batch, out_ptr: int, plan: int | None, stream: int | None):
+    _check(load_library().pq_permanent_batched(ctypes.byref(b), out_ptr, plan, stream),
+           "pq_permanent_batched")
+
+
+def pq_bs_probs(U_ptr, m, in_ptr, out_ptr, B, probs_ptr, amps_ptr, plan, stream):
+    _check(load_library().pq_bs_probs(U_ptr, m, in_ptr, out_ptr, B, probs_ptr, amps_ptr, plan,
+                                      stream), "pq_bs_probs")
+
+
+def pq_permanent_backward(b: pq_batch, grad_out_ptr, grad_mats_ptr, plan, stream):
+    _check(load_library().pq_permanent_backward(ctypes.byref(b), grad_out_ptr, grad_mats_ptr,
+                                                plan, stream), "pq_permanent_backward")
+
+
+def pq_bs_probs_backward(U_ptr, m, in_ptr, out_ptr, B, grad_probs_ptr, amps_ptr, grad_U_ptr,
+                         plan, stream):
+    _check(load_library().pq_bs_probs_backward(U_ptr, m, in_ptr, out_ptr, B, grad_probs_ptr,
+                                               amps_ptr, grad_U_ptr, plan, stream),
+           "pq_bs_probs_backward")
+
+
+def pq_clements_forward(theta_ptr, phi_ptr, m, U_ptr, stream):
+    _check(load_library().pq_clements_forward(theta_ptr, phi_ptr, m, U_ptr, stream),
+           "pq_clements_forward")
+
+
+def pq_clements_backward(theta_ptr, phi_ptr, m, U_ptr, gU_ptr, gtheta_ptr, gphi_ptr, stream):
+    _check(load_library().pq_clements_backward(theta_ptr, phi_ptr, m, U_ptr, gU_ptr, gtheta_ptr,
+                                               gphi_ptr, stream), "pq_clements_backward")
+
+
+def pq_autotune(plan: int, b: pq_batch | None, U_ptr, stream):
+    _check(load_library().pq_autotune(plan, ctypes.byref(b) if b is not None else None, U_ptr,
+                                      stream), "pq_autotune")
+
+
+def pq_plan_get_stats(plan: int) -> pq_plan_stats:
+    s = pq_plan_stats()
+    _check(load_library().pq_plan_get_stats(plan, ctypes.byref(s)), "pq_plan_get_stats")
+    return s
+
+
+def pq_probe_fp64_peak(iters: int, stream=None) -> tuple[float, float]:
+    f = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(load_library().pq_probe_fp64_peak(iters, ctypes.byref(f), ctypes.byref(ms), stream),
+           "pq_probe_fp64_peak")
+    return f.value, ms.value
+
+
+def pq_version() -> str:
+    return load_library().pq_version().decode()
+
+
+def pq_last_error() -> str:
+    return load_library().pq_last_error().decode()

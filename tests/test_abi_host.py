@@ -1,0 +1,145 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/pq.h declares, rejects bad arguments on the host, and its
+planner and Gray-code walk (the code the kernels run, compiled for the host)
+behave as the method requires (Sec. 4.2: mixed-radix Gray code whose digit
+for a row runs over 0..multiplicity)."""
+import ctypes
+import itertools
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2403_04006_gb300 import build as B
+from paper_2403_04006_gb300 import pq
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pq.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return pq.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:int|const char\*)\s+(pq_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_named_calls():
+    names = declared_functions()
+    for must in ("pq_permanent_batched", "pq_bs_probs", "pq_permanent_backward",
+                 "pq_bs_probs_backward", "pq_clements_forward", "pq_clements_backward",
+                 "pq_plan_create", "pq_plan_create_bs", "pq_plan_destroy", "pq_autotune",
+                 "pq_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_no_error(lib):
+    assert "sm_103a" in pq.pq_version()
+
+
+def test_host_argument_errors_without_gpu(lib):
+    # null arguments are rejected before any CUDA call
+    assert lib.pq_plan_create(None, None, None) == pq.PQ_ERR_ARG
+    assert lib.pq_permanent_batched(None, None, None, None) == pq.PQ_ERR_ARG
+    assert lib.pq_bs_probs(None, 4, None, None, 1, None, None, None, None) == pq.PQ_ERR_ARG
+    assert lib.pq_clements_forward(None, None, 4, None, None) == pq.PQ_ERR_ARG
+    assert "null" in pq.pq_last_error()
+
+
+class ItemInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("transposed", ctypes.c_int32), ("ndig", ctypes.c_int32), ("J", ctypes.c_int32),
+                ("terms", ctypes.c_int64), ("chunk_len", ctypes.c_int64),
+                ("chunks", ctypes.c_int64), ("radix", ctypes.c_int32 * 48),
+                ("row_of_digit", ctypes.c_int32 * 48)]
+
+
+def item_info(lib, r, c, log2=0):
+    r = np.ascontiguousarray(r, dtype=np.int32)
+    c = np.ascontiguousarray(c, dtype=np.int32)
+    info = ItemInfo()
+    rc = lib.pq_plan_item_info(len(r), len(c), r.ctypes.data_as(ctypes.c_void_p),
+                               c.ctypes.data_as(ctypes.c_void_p), log2, ctypes.byref(info))
+    return rc, info
+
+
+def side_terms(m):
+    m = [x for x in m if x > 0]
+    f = int(np.argmin(m))
+    return int(np.prod([x if i == f else x + 1 for i, x in enumerate(m)]))
+
+
+@pytest.mark.parametrize("r,c", [([1] * 12, [1] * 12), ([2, 1, 3], [1, 1, 1, 1, 1, 1]),
+                                 ([1, 1, 1, 1], [4]), ([2, 2, 2], [3, 3]), ([3], [3]),
+                                 ([0, 2, 0, 1], [1, 0, 2]), ([1] * 30, [1] * 30)])
+def test_planner_side_choice_and_term_count(lib, r, c):
+    rc, info = item_info(lib, r, c)
+    assert rc == 0
+    n = sum(r)
+    assert info.n == n
+    Tr, Tc = side_terms(r), side_terms(c)
+    assert info.terms == min(Tr, Tc)
+    assert info.transposed == (1 if Tc < Tr else 0)
+    rad = list(info.radix[:info.ndig])
+    assert rad == sorted(rad)
+    assert math.prod(rad) == info.terms
+    assert info.chunk_len == math.prod(rad[:info.J])
+    assert info.chunks * info.chunk_len == info.terms
+    # collision-free: Glynn's 2^(n-1) sign vectors
+    if all(x == 1 for x in r) and all(x == 1 for x in c):
+        assert info.terms == 2 ** (n - 1)
+
+
+def test_planner_rejects(lib):
+    assert item_info(lib, [1, 2], [1, 1])[0] == pq.PQ_ERR_ARG  # 3 != 2
+    assert item_info(lib, [-1, 2], [1])[0] == pq.PQ_ERR_ARG
+    # one column repeated 41 times is the cheap side to sum, which leaves 41
+    # product-side columns: above PQ_MAX_PRODUCT_COLS
+    assert item_info(lib, [1] * 41, [41])[0] == pq.PQ_ERR_UNSUPPORTED
+    assert item_info(lib, [1] * 49, [1] * 49)[0] == pq.PQ_ERR_UNSUPPORTED  # n > PQ_MAX_N
+    rc, info = item_info(lib, [0, 0], [0])
+    assert rc == 0 and info.n == 0
+
+
+@pytest.mark.parametrize("radix", [[2], [3], [2, 2, 2], [2, 3, 4], [3, 2, 4], [2, 2, 3, 3],
+                                   [4, 4], [15], [2] * 10, [5, 3, 2]])
+def test_gray_walk_visits_every_code_once_with_unit_steps(lib, radix):
+    total = math.prod(radix)
+    steps = total - 1
+    rad = np.asarray(radix, dtype=np.int32)
+    dig = np.zeros(max(steps, 1), dtype=np.int32)
+    dr = np.zeros(max(steps, 1), dtype=np.int32)
+    rc = lib.pq_gray_walk(rad.ctypes.data_as(ctypes.c_void_p), len(radix), steps,
+                          dig.ctypes.data_as(ctypes.c_void_p), dr.ctypes.data_as(ctypes.c_void_p))
+    assert rc == 0
+    g = [0] * len(radix)
+    seen = {tuple(g)}
+    for s in range(steps):
+        d, u = int(dig[s]), int(dr[s])
+        assert u in (1, -1)
+        g[d] += u
+        assert 0 <= g[d] < radix[d]
+        seen.add(tuple(g))
+    assert len(seen) == total
+    assert seen == set(itertools.product(*[range(x) for x in radix]))
+
+
+def test_gray_walk_rejects_too_many_steps(lib):
+    rad = np.asarray([2, 3], dtype=np.int32)
+    buf = np.zeros(16, dtype=np.int32)
+    assert lib.pq_gray_walk(rad.ctypes.data_as(ctypes.c_void_p), 2, 6,
+                            buf.ctypes.data_as(ctypes.c_void_p),
+                            buf.ctypes.data_as(ctypes.c_void_p)) == pq.PQ_ERR_ARG

@@ -1,0 +1,61 @@
+"""The bench's multi-rank bookkeeping on CPU with gloo (world size 2): every
+rank runs its own batch (weak scaling, no data-path collective); the timed
+region is closed by a barrier, the time is the maximum over ranks and the
+throughput counts the units of all ranks."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    r, w = bench.init_dist("gloo")
+    assert (r, w) == (rank, world)
+    my_seconds = 1.0 + rank  # rank 1 is the slower one
+    bench.barrier()
+    slowest = bench.max_over_ranks(my_seconds)
+    rate = bench.whole_job_rate(1000.0, w, slowest)
+    q.put((rank, slowest, rate))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_weak_scaling_rate():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, slowest, rate in got:
+        assert slowest == 2.0          # max over ranks
+        assert rate == 1000.0 * 2 / 2.0  # all ranks' units / slowest time
+
+
+def test_single_process_helpers():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.whole_job_rate(10.0, 1, 2.0) == 5.0
+    assert bench.max_over_ranks(3.0) == 3.0  # no process group: identity

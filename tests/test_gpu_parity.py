@@ -1,0 +1,366 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle
+on identical seeded inputs.
+
+Tolerances (stated requirement of the path): relative error <= 1e-10 for
+n <= 20, <= 1e-8 at n = 30, gradients within 1e-7 (max-norm, relative to the
+reference's max-norm).  Expected values come from the oracle's gold mode
+(double-double throughout), whose own error bound is checked to be far below
+these tolerances; exact zeros (Hong-Ou-Mandel) are compared absolutely.
+"""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2403_04006_gb300 import api, pq  # noqa: E402
+from paper_2403_04006_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "golden"))
+from make_golden import read_matrix_file  # noqa: E402
+
+TOL = 1e-10
+TOL30 = 1e-8
+TOLG = 1e-7
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pq.load_library()
+    return torch.device("cuda:0")
+
+
+def rel_err(x, ref):
+    x = np.asarray(x)
+    ref = np.asarray(ref)
+    return np.abs(x - ref) / np.abs(ref)
+
+
+def random_parts(n, rng, maxpart=3):
+    out, left = [], n
+    while left:
+        p = min(int(rng.integers(1, maxpart + 1)), left)
+        out.append(p)
+        left -= p
+    return out
+
+
+def random_items(count, nmin, nmax, rng, maxpart=3):
+    items = []
+    for _ in range(count):
+        n = int(rng.integers(nmin, nmax + 1))
+        r = random_parts(n, rng, maxpart)
+        c = random_parts(n, rng, maxpart)
+        B = (rng.standard_normal((len(r), len(c))) + 1j * rng.standard_normal((len(r), len(c))))
+        B /= math.sqrt(2 * n)
+        items.append((B, r, c))
+    return items
+
+
+def oracle_items(items):
+    return np.array([O.perm_ryser(B, r, c, gold=True) for B, r, c in items])
+
+
+def gpu_perms(pb, dev, method="batched", use_graph=False, chunk_log2=0):
+    db = api.DeviceBatch(pb, dev)
+    plan = api.Plan.for_batch(pb, method=method, use_graph=use_graph, chunk_log2=chunk_log2)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        out = api.permanent_batched(db, plan)
+    s.synchronize()
+    return out.cpu().numpy(), plan
+
+
+# ------------------------------------------------------------------ forward
+def test_random_batch_with_multiplicities(dev):
+    rng = np.random.default_rng(101)
+    items = random_items(300, 1, 14, rng)
+    pb = W.pack_batch(items)
+    ref = oracle_items(items)
+    got_b, _ = gpu_perms(pb, dev, "batched")
+    got_p, _ = gpu_perms(pb, dev, "plain")
+    assert rel_err(got_b, ref).max() <= TOL
+    # same plan layout -> same partial sums in the same order -> same bits
+    assert np.array_equal(got_b, got_p)
+
+
+@pytest.mark.parametrize("chunk_log2", [1, 3, 6, 12])
+def test_chunking_does_not_change_results(dev, chunk_log2):
+    rng = np.random.default_rng(202)
+    items = random_items(64, 6, 16, rng)
+    pb = W.pack_batch(items)
+    ref = oracle_items(items)
+    got, _ = gpu_perms(pb, dev, chunk_log2=chunk_log2)
+    assert rel_err(got, ref).max() <= TOL
+
+
+def test_edge_cases(dev):
+    rng = np.random.default_rng(303)
+    items, want = [], []
+    # n = 0: empty base and all-zero multiplicities -> per = 1
+    items.append((np.zeros((0, 0)), [], []))
+    want.append(1.0)
+    items.append((rng.standard_normal((2, 3)) + 0j, [0, 0], [0, 0, 0]))
+    want.append(1.0)
+    # n = 1
+    items.append((np.array([[0.3 - 0.7j]]), [1], [1]))
+    want.append(0.3 - 0.7j)
+    # 1 x 1 base repeated: per = n! a^n
+    a = 0.8 + 0.35j
+    for n in (2, 3, 5, 9, 12):
+        items.append((np.array([[a]]), [n], [n]))
+        want.append(math.factorial(n) * a ** n)
+    # all ones and ones minus identity (derangements)
+    for n in (4, 9, 13):
+        items.append((np.ones((n, n)) + 0j, [1] * n, [1] * n))
+        want.append(float(math.factorial(n)))
+    d = [1, 0]
+    for i in range(2, 14):
+        d.append((i - 1) * (d[-1] + d[-2]))
+    for n in (5, 10, 13):
+        items.append((np.ones((n, n)) - np.eye(n) + 0j, [1] * n, [1] * n))
+        want.append(float(d[n]))
+    # zero-multiplicity rows/columns among live ones
+    B = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    items.append((B, [2, 0, 1, 0], [0, 1, 0, 2]))
+    want.append(O.perm_ryser(B[[0, 2]][:, [1, 3]], [2, 1], [1, 2], gold=True))
+    # widest product side: 2 rows repeated 20 times against 40 single columns
+    B = (rng.standard_normal((2, 40)) + 1j * rng.standard_normal((2, 40))) / 4
+    items.append((B, [20, 20], [1] * 40))
+    want.append(O.perm_ryser(B, [20, 20], [1] * 40, gold=True))
+    # one row, one column, tall and wide bases
+    B = rng.standard_normal((1, 5)) + 1j * rng.standard_normal((1, 5))
+    items.append((B, [5], [1] * 5))
+    want.append(O.perm_ryser(B, [5], [1] * 5, gold=True))
+    B = rng.standard_normal((6, 1)) + 1j * rng.standard_normal((6, 1))
+    items.append((B, [1] * 6, [6]))
+    want.append(O.perm_ryser(B, [1] * 6, [6], gold=True))
+    pb = W.pack_batch(items)
+    got, _ = gpu_perms(pb, dev)
+    want = np.array(want, dtype=np.complex128)
+    for (B, r, c), g, w in zip(items, got, want):
+        # J_n and J - I cancel heavily in any inclusion-exclusion sum: allow
+        # the a-priori rounding bound of the Glynn sum as well as TOL
+        n = int(sum(r))
+        bound = 0.0
+        if 0 < n <= 14:
+            bound = 8 * n * 2.0 ** -53 * glynn_abs_sum(np.repeat(np.repeat(B, r, 0), c, 1))
+        assert abs(g - w) <= max(TOL * abs(w), bound), (n, g, w)
+
+
+def glynn_abs_sum(A):
+    """2^-(n-1) sum over sign vectors (first fixed) of prod_j |sum_i d_i a_ij|."""
+    n = A.shape[0]
+    if n == 1:
+        return abs(A[0, 0])
+    signs = np.array(np.meshgrid(*[[1.0, -1.0]] * (n - 1), indexing="ij")).reshape(n - 1, -1).T
+    d = np.concatenate([np.ones((signs.shape[0], 1)), signs], axis=1)
+    return float(np.prod(np.abs(d @ A), axis=1).sum()) / 2 ** (n - 1)
+
+
+def test_argument_errors_on_device(dev):
+    pb = W.pack_batch([(np.ones((2, 2)) + 0j, [1, 2], [1, 1])])  # 3 != 2
+    with pytest.raises(pq.PQError) as e:
+        api.Plan.for_batch(pb)
+    assert e.value.code == pq.PQ_ERR_ARG
+
+
+def test_bs_small_probabilities(dev):
+    """Workload 1: m = 8, |1,1,1,1,0,0,0,0>, all 330 outputs; sum p = 1."""
+    U, s, t = W.bs_small()
+    p_ref, a_ref = O.bs_probs(U, s, t, gold=True)
+    for method in ("batched", "plain"):
+        plan = api.Plan.for_bs(8, s, t, method=method)
+        p, a = api.bs_probs(torch.from_numpy(U).to(dev), torch.from_numpy(s).to(dev),
+                            torch.from_numpy(t).to(dev), plan)
+        torch.cuda.synchronize()
+        p, a = p.cpu().numpy(), a.cpu().numpy()
+        assert abs(p.sum() - 1.0) <= 1e-13
+        assert rel_err(a, a_ref).max() <= TOL
+        assert rel_err(p, p_ref).max() <= 2 * TOL
+    # the convenience path without a plan
+    p2, _ = api.bs_probs(torch.from_numpy(U).to(dev), torch.from_numpy(s).to(dev),
+                         torch.from_numpy(t).to(dev), None)
+    assert rel_err(p2.cpu().numpy(), p_ref).max() <= 2 * TOL
+
+
+def test_hong_ou_mandel(dev):
+    U = O.beamsplitter_block(math.pi / 4, 0.4)
+    s = np.array([1, 1], dtype=np.int32)
+    t = np.array([[1, 1], [2, 0], [0, 2]], dtype=np.int32)
+    p, _ = api.bs_probs(torch.from_numpy(U).to(dev), torch.from_numpy(s).to(dev),
+                        torch.from_numpy(t).to(dev), api.Plan.for_bs(2, s, t))
+    p = p.cpu().numpy()
+    assert abs(p[0]) <= 1e-16
+    assert abs(p[1] - 0.5) <= 1e-15 and abs(p[2] - 0.5) <= 1e-15
+
+
+def test_bs_batched_workload(dev):
+    """Workload 3: m = 24, 12 photons, 4096 patterns (half with collisions)."""
+    U, s, t = W.bs_batched()
+    p_ref, a_ref = O.bs_probs(U, s, t, gold=True)
+    Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))
+    for method, graph in (("batched", False), ("batched", True), ("plain", False)):
+        plan = api.Plan.for_bs(24, s, t, method=method, use_graph=graph)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            p, a = api.bs_probs(Ud, sd, td, plan)
+            if graph:  # replay the captured graph
+                p, a = api.bs_probs(Ud, sd, td, plan)
+        st.synchronize()
+        assert rel_err(a.cpu().numpy(), a_ref).max() <= TOL
+        assert rel_err(p.cpu().numpy(), p_ref).max() <= 2 * TOL
+
+
+def test_ragged_workload_sampled(dev):
+    """Workload 4 at full size (65536 permanents, one persistent launch),
+    every 16th item checked against the oracle plus every item of n = 20."""
+    pb = W.ragged()
+    got, plan = gpu_perms(pb, dev, use_graph=True)
+    assert np.isfinite(got).all()
+    ns = np.array([int(pb.row_mult[pb.row_off[b]:pb.row_off[b] + pb.k[b]].sum())
+                   for b in range(pb.batch)])
+    idx = sorted(set(range(0, pb.batch, 16)) | set(np.nonzero(ns == 20)[0][:256].tolist()))
+    sub = pb.subset(idx)
+    ref = O.perm_batch(sub.mats, sub.mat_off, sub.k, sub.l, sub.row_mult, sub.row_off,
+                       sub.col_mult, sub.col_off, gold=True)
+    assert rel_err(got[idx], ref).max() <= TOL
+    assert plan.stats()["launches_forward"] == 1
+
+
+def test_single_large_n30(dev):
+    """Workload 2: n = 30 (2^29 Gray-code terms) against the stored gold value."""
+    A, vals = read_matrix_file(os.path.join(HERE, "golden", "single_large_n30.txt"))
+    assert vals["bound_gold"] < 1e-12 * abs(vals["per_gold"])
+    pb = W.pack_batch([(A, [1] * 30, [1] * 30)])
+    got, plan = gpu_perms(pb, dev)
+    assert plan.stats()["terms"] == 2 ** 29
+    assert rel_err(got[0], vals["per_gold"]) <= TOL30
+    # the generator still produces this workload
+    assert np.abs(W.single_large(30) - A).max() <= 1e-12
+
+
+def test_results_are_deterministic(dev):
+    U, s, t = W.bs_batched()
+    plan = api.Plan.for_bs(24, s, t)
+    Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))
+    p1, a1 = api.bs_probs(Ud, sd, td, plan)
+    p2, a2 = api.bs_probs(Ud, sd, td, plan)
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2) and torch.equal(p1, p2)
+
+
+def test_autotune_then_parity(dev):
+    U, s, t = W.bs_batched()
+    Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))
+    plan = api.Plan.for_bs(24, s, t)
+    plan.autotune(U=Ud)
+    p, a = api.bs_probs(Ud, sd, td, plan)
+    p_ref, a_ref = O.bs_probs(U, s, t, gold=True)
+    assert rel_err(a.cpu().numpy(), a_ref).max() <= TOL
+
+
+# ------------------------------------------------------------------ backward
+def test_permanent_backward_vs_minors(dev):
+    rng = np.random.default_rng(404)
+    items = random_items(60, 1, 10, rng)
+    items.append((np.array([[0.5 + 0.1j]]), [1], [1]))
+    items.append((np.zeros((0, 0)), [], []))
+    pb = W.pack_batch(items)
+    db = api.DeviceBatch(pb, dev)
+    gout = (rng.standard_normal(pb.batch) + 1j * rng.standard_normal(pb.batch))
+    for method in ("batched", "plain"):
+        plan = api.Plan.for_batch(pb, method=method)
+        g = api.permanent_backward(db, torch.from_numpy(gout).to(dev), plan).cpu().numpy()
+        for b, (B, r, c) in enumerate(items):
+            if B.size == 0:
+                continue
+            ref = gout[b] * np.conj(O.perm_grad(B, r, c, gold=True))
+            o = int(pb.mat_off[b])
+            got = g[o:o + B.size].reshape(B.shape)
+            assert np.abs(got - ref).max() <= TOLG * max(np.abs(ref).max(), 1e-300)
+
+
+def test_permanent_gradcheck(dev):
+    rng = np.random.default_rng(505)
+    items = random_items(4, 2, 5, rng)
+    pb = W.pack_batch(items)
+    db = api.DeviceBatch(pb, dev)
+    plan = api.Plan.for_batch(pb)
+    mats = torch.from_numpy(pb.mats).to(dev).requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda x: api.Permanent.apply(x, db, plan), (mats,),
+                                    eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+def test_clements_forward(dev):
+    th, ph, s, t = W.gradient_workload()
+    U = api.clements_forward(torch.from_numpy(th).to(dev), torch.from_numpy(ph).to(dev), 16)
+    ref = O.clements_unitary(th, ph, 16)
+    assert np.abs(U.cpu().numpy() - ref).max() <= 1e-13
+
+
+def test_gradient_workload(dev):
+    """Workload 5: Clements mesh (m = 16, 120 beamsplitters) -> probabilities of
+    1024 patterns with 8 photons -> L = sum p; dL/dU against Laplace-minor
+    permanents, dL/d(theta, phi) against the oracle's chain rule and against
+    central finite differences (h = 1e-6) of the oracle's L."""
+    th, ph, s, t = W.gradient_workload()
+    thd = torch.from_numpy(th).to(dev).requires_grad_(True)
+    phd = torch.from_numpy(ph).to(dev).requires_grad_(True)
+    sd, td = torch.from_numpy(s).to(dev), torch.from_numpy(t).to(dev)
+    plan = api.Plan.for_bs(16, s, t)
+    U = api.ClementsMesh.apply(thd, phd, 16)
+    U.retain_grad()
+    L = api.BSProbs.apply(U, sd, td, plan).sum()
+    L.backward()
+    torch.cuda.synchronize()
+    Uref = O.clements_unitary(th, ph, 16)
+    p_ref, _ = O.bs_probs(Uref, s, t, gold=True)
+    assert abs(L.item() - p_ref.sum()) <= TOL * p_ref.sum()
+    G_ref = O.bs_grad_U(Uref, s, t, np.ones(len(t)), gold=True)
+    G = U.grad.cpu().numpy()
+    assert np.abs(G - G_ref).max() <= TOLG * np.abs(G_ref).max()
+    gt_ref, gp_ref = O.clements_grad(th, ph, 16, G_ref)
+    gt, gp = thd.grad.cpu().numpy(), phd.grad.cpu().numpy()
+    scale = max(np.abs(gt_ref).max(), np.abs(gp_ref).max())
+    assert np.abs(gt - gt_ref).max() <= TOLG * scale
+    assert np.abs(gp - gp_ref).max() <= TOLG * scale
+
+    def L_oracle(a, b):
+        return O.bs_probs(O.clements_unitary(a, b, 16), s, t)[0].sum()
+
+    h = 1e-6
+    for k in (0, 7, 8, 59, 119):
+        e = np.zeros(120)
+        e[k] = h
+        fd_t = (L_oracle(th + e, ph) - L_oracle(th - e, ph)) / (2 * h)
+        fd_p = (L_oracle(th, ph + e) - L_oracle(th, ph - e)) / (2 * h)
+        assert abs(gt[k] - fd_t) <= TOLG * scale
+        assert abs(gp[k] - fd_p) <= TOLG * scale
+
+
+def test_bs_backward_plain_matches_batched(dev):
+    th, ph, s, t = W.gradient_workload()
+    U = torch.from_numpy(O.clements_unitary(th, ph, 16)).to(dev)
+    sd, td = torch.from_numpy(s).to(dev), torch.from_numpy(t).to(dev)
+    g = torch.linspace(0.5, 1.5, len(t), dtype=torch.float64, device=dev)
+    outs = []
+    for method in ("batched", "plain"):
+        plan = api.Plan.for_bs(16, s, t, method=method)
+        p, a = api.bs_probs(U, sd, td, plan)
+        outs.append(api.bs_probs_backward(U, sd, td, g, a, plan).cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_fp64_probe_runs(dev):
+    flops, ms = api.probe_fp64_peak(1 << 12)
+    assert flops > 1e11 and ms > 0
