@@ -6,8 +6,10 @@
 //   G_ij = d per / d b_ij = 2^{-(n-1)} sum_t w_t x_i(t) Q_j(t),
 //   Q_j  = c_j S_j^{c_j - 1} prod_{j' != j} S_{j'}^{c_{j'}},
 // which counts every copy of b_ij in the expanded matrix.  Q_j comes from
-// prefix and suffix products of the column sums (no division, so S_j = 0 is
-// harmless).
+// prefix and suffix products of the column powers (no division, so S_j = 0
+// is harmless).  Product columns arrive sorted by non-increasing
+// multiplicity, so the columns with c_j >= 2 are the first n2 and the loops
+// are split at n2 instead of testing c_j per column.
 //
 // Accumulation per thread over one chunk: A_j = sum_t w_t Q_j(t).  Rows whose
 // x_i is constant in the chunk (high digits, rows without a digit) contribute
@@ -19,6 +21,10 @@
 // one permanent are summed in task order by the warp that finishes last, and
 // the result is multiplied by the upstream gradient (PyTorch convention:
 // grad_b = grad_per * conj(G)).
+//
+// As in the forward kernel, every per-lane array lives in shared memory,
+// lane-major, and every loop over columns is a runtime loop, so the FP64 pipe
+// (the only loaded resource on GB300) sees no predicated or speculative work.
 #include <cuda_runtime.h>
 
 #include "pq_device.cuh"
@@ -26,133 +32,149 @@
 
 namespace pqi {
 
-__host__ __device__ inline int bwd_warp_smem_bytes(int kmax, int lmax, int jb)
+// Per-warp shared memory (ld = product-column bound, jb = low-digit bound).
+__host__ __device__ inline int bwd_warp_smem_bytes(int kmax, int ld, int jb)
 {
-    long bytes = 16L * (kmax * lmax + lmax + 64L * lmax + 32L * jb * lmax) + 8L * 32 +
-                 4L * (32L * kmax + 16 + lmax + kmax);
+    long bytes = 16L * (kmax * ld + ld + 5L * 32 * ld + 32L * jb * ld) + 8L * 32 +
+                 4L * (32L * kmax + 16 + ld + kmax);
     return (int)((bytes + 15) & ~15L);
 }
 
-template <int LMAX>
 struct BwdSmem {
-    double2* M;       // kmax x LMAX
-    double2* base;    // LMAX
-    double2* A;       // LMAX x 32 (lane-major)
-    double2* P;       // LMAX x 32
-    double2* C;       // JB x LMAX x 32
+    double2* M;       // kmax x ld
+    double2* base;    // ld
+    double2* S;       // ld x 32 (lane-major)
+    double2* A;       // ld x 32
+    double2* P;       // ld x 32
+    double2* PW;      // ld x 32
+    double2* FULL;    // ld x 32
+    double2* C;       // jb x ld x 32
     double* wh;       // 32
     int32_t* x;       // kmax x 32
     int32_t* lowrow;  // 16
-    int32_t* cm;      // LMAX
+    int32_t* cm;      // ld
     int32_t* rowdig;  // kmax: low digit of each row, or -1
-    __device__ BwdSmem(unsigned char* raw, int kmax, int jb)
+    int ld;
+    __device__ BwdSmem(unsigned char* raw, int kmax, int ld_, int jb)
     {
+        ld = ld_;
         M = reinterpret_cast<double2*>(raw);
-        base = M + kmax * LMAX;
-        A = base + LMAX;
-        P = A + LMAX * 32;
-        C = P + LMAX * 32;
-        wh = reinterpret_cast<double*>(C + jb * LMAX * 32);
+        base = M + kmax * ld;
+        S = base + ld;
+        A = S + 32 * ld;
+        P = A + 32 * ld;
+        PW = P + 32 * ld;
+        FULL = PW + 32 * ld;
+        C = FULL + 32 * ld;
+        wh = reinterpret_cast<double*>(C + 32 * jb * ld);
         x = reinterpret_cast<int32_t*>(wh + 32);
         lowrow = x + kmax * 32;
         cm = lowrow + 16;
-        rowdig = cm + LMAX;
+        rowdig = cm + ld;
     }
 };
 
-// A_j +-= w Q_j for the current column sums (prefix products kept in P).
-template <int LMAX, bool NEG>
-__device__ __forceinline__ void bwd_term(const double2 (&S)[LMAX], int l, int n,
-                                         const int32_t* cm, double w, double2* P, double2* A,
-                                         int lane)
+__device__ __forceinline__ void acc_scaled(double2* a, double s, double2 q)
 {
-    const double ws = NEG ? -w : w;
-    if (n == 1) {  // per = b: dper/db = 1
-        double2 a = A[lane];
-        a.x = __dadd_rn(a.x, ws);
-        A[lane] = a;
+    double2 v = *a;
+    v.x = __fma_rn(s, q.x, v.x);
+    v.y = __fma_rn(s, q.y, v.y);
+    *a = v;
+}
+
+// A_j += ws * Q_j for this lane's column sums.  All pointers are lane-offset
+// with stride 32.  n2 = number of leading columns with c_j >= 2.
+__device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* PW, double2* FULL,
+                                         double2* A, int l, int n2, const int32_t* cm, double ws)
+{
+    if (l == 1) {
+        if (n2 == 0) {  // n = 1: d per / d b = 1
+            A[0].x = __dadd_rn(A[0].x, ws);
+            return;
+        }
+        double2 q = S[0];  // c_0 S_0^{c_0 - 1}
+#pragma unroll 1
+        for (int e = 2; e < cm[0]; ++e)
+            q = cmul(q, S[0]);
+        acc_scaled(A, ws * (double)cm[0], q);
         return;
     }
-    // prefix: P_j = prod_{j' < j} S_{j'}^{c_{j'}}
-    double2 run = make_double2(1.0, 0.0);
-#pragma unroll
-    for (int j = 0; j < LMAX; ++j) {
-        if (j < l) {
-            if (j > 0)
-                P[j * 32 + lane] = run;
-            const int c = cm[j];
-            int e0 = 0;
-            if (j == 0) {
-                run = S[0];
-                e0 = 1;
-            }
-            for (int e = e0; e < c; ++e)
-                run = cmul(run, S[j]);
+    // powers of the repeated columns
+#pragma unroll 1
+    for (int j = 0; j < n2; ++j) {
+        const double2 s = S[j * 32];
+        double2 pw = s;
+#pragma unroll 1
+        for (int e = 2; e < cm[j]; ++e)
+            pw = cmul(pw, s);
+        PW[j * 32] = pw;
+        FULL[j * 32] = cmul(pw, s);
+    }
+    // prefix P_j = prod_{j' < j} S_{j'}^{c_{j'}}, j = 1 .. l-1
+    double2 run = (n2 > 0) ? FULL[0] : S[0];
+    P[32] = run;
+    const int na = n2 < l - 1 ? n2 : l - 1;  // repeated columns among 1 .. l-2
+#pragma unroll 1
+    for (int j = 1; j < na; ++j) {
+        run = cmul(run, FULL[j * 32]);
+        P[(j + 1) * 32] = run;
+    }
+#pragma unroll 1
+    for (int j = (na > 1 ? na : 1); j < l - 1; ++j) {
+        run = cmul(run, S[j * 32]);
+        P[(j + 1) * 32] = run;
+    }
+    // suffix pass, last column first
+    double2 sf;
+    {
+        const int j = l - 1;
+        double2 q = P[j * 32];
+        if (j < n2) {
+            q = cmul(q, PW[j * 32]);
+            acc_scaled(A + j * 32, ws * (double)cm[j], q);
+            sf = FULL[j * 32];
+        } else {
+            acc_scaled(A + j * 32, ws, q);
+            sf = S[j * 32];
         }
     }
-    // suffix pass: Q_j = c_j S_j^{c_j-1} P_j Sf_j, Sf_j = prod_{j' > j} S_{j'}^{c_{j'}}
-    double2 sf = make_double2(1.0, 0.0);
-    bool sf_one = true;
-#pragma unroll
-    for (int j = LMAX - 1; j >= 0; --j) {
-        if (j < l) {
-            const int c = cm[j];
-            double2 q;
-            bool q_one;
-            if (j == 0) {
-                q = sf;
-                q_one = sf_one;
-            } else {
-                q = P[j * 32 + lane];
-                q_one = false;
-                if (!sf_one)
-                    q = cmul(q, sf);
-            }
-            for (int e = 1; e < c; ++e) {
-                if (q_one) {
-                    q = S[j];
-                    q_one = false;
-                } else {
-                    q = cmul(q, S[j]);
-                }
-            }
-            double2 a = A[j * 32 + lane];
-            const double wc = (c > 1) ? ws * (double)c : ws;
-            if (q_one) {
-                a.x = __dadd_rn(a.x, wc);
-            } else {
-                a.x = __fma_rn(wc, q.x, a.x);
-                a.y = __fma_rn(wc, q.y, a.y);
-            }
-            A[j * 32 + lane] = a;
-            if (j > 0) {
-                for (int e = 0; e < c; ++e) {
-                    if (sf_one) {
-                        sf = S[j];
-                        sf_one = false;
-                    } else {
-                        sf = cmul(sf, S[j]);
-                    }
-                }
-            }
-        }
+    // columns l-2 .. 1 with c_j = 1
+#pragma unroll 1
+    for (int j = l - 2; j >= 1 && j >= n2; --j) {
+        const double2 q = cmul(P[j * 32], sf);
+        acc_scaled(A + j * 32, ws, q);
+        sf = cmul(sf, S[j * 32]);
+    }
+    // columns min(n2, l-1) - 1 .. 1 with c_j >= 2
+#pragma unroll 1
+    for (int j = (n2 < l - 1 ? n2 : l - 1) - 1; j >= 1; --j) {
+        double2 q = cmul(P[j * 32], sf);
+        q = cmul(q, PW[j * 32]);
+        acc_scaled(A + j * 32, ws * (double)cm[j], q);
+        sf = cmul(sf, FULL[j * 32]);
+    }
+    // column 0: Q_0 = c_0 S_0^{c_0 - 1} * prod_{j > 0}
+    if (n2 > 0) {
+        const double2 q = cmul(sf, PW[0]);
+        acc_scaled(A, ws * (double)cm[0], q);
+    } else {
+        acc_scaled(A, ws, sf);
     }
 }
 
-template <int LMAX>
-__device__ void bwd_stage(const BwdArgs& a, const PermDesc& D, const MetaView& mv,
-                          BwdSmem<LMAX>& sm, int lane)
+__device__ void bwd_stage(const BwdArgs& a, const PermDesc& D, const MetaView& mv, BwdSmem& sm,
+                          int lane)
 {
     const int k = D.k, l = D.l;
     for (int e = lane; e < k * l; e += kWarp) {
-        int i = e / l, j = e - i * l;
-        int64_t off = D.src_off + (int64_t)mv.ridx[i] * D.si + (int64_t)mv.cidx[j] * D.sj;
-        sm.M[i * LMAX + j] = a.src[off];
+        const int i = e / l, j = e - i * l;
+        const int64_t off = D.src_off + (int64_t)mv.ridx[i] * D.si + (int64_t)mv.cidx[j] * D.sj;
+        sm.M[i * sm.ld + j] = a.src[off];
     }
     for (int d = lane; d < D.J; d += kWarp)
         sm.lowrow[d] = mv.drow[d];
-    for (int j = lane; j < LMAX; j += kWarp)
-        sm.cm[j] = (j < l) ? mv.cmul[j] : 0;
+    for (int j = lane; j < l; j += kWarp)
+        sm.cm[j] = mv.cmul[j];
     for (int i = lane; i < k; i += kWarp) {
         int dg = -1;
         for (int d = 0; d < D.J; ++d)
@@ -164,8 +186,8 @@ __device__ void bwd_stage(const BwdArgs& a, const PermDesc& D, const MetaView& m
     for (int j = lane; j < l; j += kWarp) {
         double2 s = make_double2(0.0, 0.0);
         for (int i = 0; i < k; ++i) {
-            double r = (double)mv.rmul[i];
-            double2 b = sm.M[i * LMAX + j];
+            const double r = (double)mv.rmul[i];
+            const double2 b = sm.M[i * sm.ld + j];
             s.x = __fma_rn(r, b.x, s.x);
             s.y = __fma_rn(r, b.y, s.y);
         }
@@ -174,53 +196,49 @@ __device__ void bwd_stage(const BwdArgs& a, const PermDesc& D, const MetaView& m
     __syncwarp();
 }
 
-template <int LMAX>
-__device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem<LMAX>& sm, int& staged,
-                         int lane, int jb)
+__device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& staged, int lane)
 {
     const PermDesc D = a.desc[t.perm];
     const MetaView mv = meta_view(a.meta, D);
-    const int k = D.k, l = D.l, n = D.n, J = D.J, ndig = D.ndig;
+    const int k = D.k, l = D.l, J = D.J, ndig = D.ndig;
     const int kl = k * l;
     double* slot = a.gpart + 2 * (a.gpart_off[t.perm] + (int64_t)t.part * kl);
 
-    if (D.trivial) {
-        // nothing depends on the matrix: zero gradient
-        for (int e = lane; e < kl; e += kWarp) {
-            slot[2 * e] = 0.0;
-            slot[2 * e + 1] = 0.0;
-        }
-    } else {
+    if (!D.trivial) {
         if (staged != t.perm) {
             __syncwarp();
-            bwd_stage<LMAX>(a, D, mv, sm, lane);
+            bwd_stage(a, D, mv, sm, lane);
             staged = t.perm;
         }
         const int64_t chunk0 = (int64_t)t.part * kWarp;
         const bool active = chunk0 + lane < D.nchunks;
         int64_t c = active ? (chunk0 + lane) : 0;
-        double2 S[LMAX];
-#pragma unroll
-        for (int j = 0; j < LMAX; ++j)
-            S[j] = (j < l) ? sm.base[j] : make_double2(0.0, 0.0);
+        double2* S = sm.S + lane;
+        double2* A = sm.A + lane;
+#pragma unroll 1
+        for (int j = 0; j < l; ++j) {
+            S[j * 32] = sm.base[j];
+            A[j * 32] = make_double2(0.0, 0.0);
+        }
         for (int i = 0; i < k; ++i)
             sm.x[i * 32 + lane] = mv.rmul[i];
         uint64_t whigh_u = 1;
         int gpar = 0;
+#pragma unroll 1
         for (int d = J; d < ndig; ++d) {
-            int rad = mv.drad[d];
-            int g = (int)(c % rad);
+            const int rad = mv.drad[d];
+            const int g = (int)(c % rad);
             c /= rad;
             const int row = mv.drow[d];
-            const double2* Mr = sm.M + row * LMAX;
-            const double coef = -2.0 * (double)g;
-#pragma unroll
-            for (int j = 0; j < LMAX; ++j) {
-                if (j < l) {
-                    double2 b = Mr[j];
-                    S[j].x = __fma_rn(coef, b.x, S[j].x);
-                    S[j].y = __fma_rn(coef, b.y, S[j].y);
-                }
+            const double2* Mr = sm.M + row * sm.ld;
+            const double coef = (double)(-2 * g);
+#pragma unroll 1
+            for (int j = 0; j < l; ++j) {
+                const double2 b = Mr[j];
+                double2 s = S[j * 32];
+                s.x = __fma_rn(coef, b.x, s.x);
+                s.y = __fma_rn(coef, b.y, s.y);
+                S[j * 32] = s;
             }
             sm.x[row * 32 + lane] = mv.rmul[row] - 2 * g;
             if (g) {
@@ -232,12 +250,13 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem<LMAX>& sm, int
         if (gpar & 1)
             whigh = -whigh;
         sm.wh[lane] = whigh;
-        for (int j = 0; j < l; ++j)
-            sm.A[j * 32 + lane] = make_double2(0.0, 0.0);
         for (int e = 0; e < J * l; ++e) {
             const int d = e / l, j = e - d * l;
-            sm.C[(d * LMAX + j) * 32 + lane] = make_double2(0.0, 0.0);
+            sm.C[(d * sm.ld + j) * 32 + lane] = make_double2(0.0, 0.0);
         }
+        int n2 = 0;
+        while (n2 < l && sm.cm[n2] >= 2)
+            ++n2;
 
         LowWalk wk;
         wk.v = 0;
@@ -251,30 +270,29 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem<LMAX>& sm, int
         }
         double wlow = 1.0;
         const int64_t L = D.L;
+#pragma unroll 1
         for (int64_t s = 0; s < L; ++s) {
-            if (s & 1)
-                bwd_term<LMAX, true>(S, l, n, sm.cm, wlow, sm.P, sm.A, lane);
-            else
-                bwd_term<LMAX, false>(S, l, n, sm.cm, wlow, sm.P, sm.A, lane);
+            bwd_term(S, sm.P + lane, sm.PW + lane, sm.FULL + lane, A, l, n2, sm.cm,
+                     (s & 1) ? -wlow : wlow);
             if (s + 1 < L) {
                 int up;
                 const int d = low_step(wk, up);
                 const int row = sm.lowrow[d];
                 const double delta = up > 0 ? -2.0 : 2.0;
-                const double2* Mr = sm.M + row * LMAX;
-                double2* Cd = sm.C + d * LMAX * 32;
-#pragma unroll
-                for (int j = 0; j < LMAX; ++j) {
-                    if (j < l) {
-                        double2 b = Mr[j];
-                        S[j].x = __fma_rn(delta, b.x, S[j].x);
-                        S[j].y = __fma_rn(delta, b.y, S[j].y);
-                        double2 av = sm.A[j * 32 + lane];
-                        double2 cv = Cd[j * 32 + lane];
-                        cv.x = __fma_rn(delta, av.x, cv.x);
-                        cv.y = __fma_rn(delta, av.y, cv.y);
-                        Cd[j * 32 + lane] = cv;
-                    }
+                const double2* Mr = sm.M + row * sm.ld;
+                double2* Cd = sm.C + d * sm.ld * 32 + lane;
+#pragma unroll 1
+                for (int j = 0; j < l; ++j) {
+                    const double2 b = Mr[j];
+                    double2 sv = S[j * 32];
+                    sv.x = __fma_rn(delta, b.x, sv.x);
+                    sv.y = __fma_rn(delta, b.y, sv.y);
+                    S[j * 32] = sv;
+                    const double2 av = A[j * 32];
+                    double2 cv = Cd[j * 32];
+                    cv.x = __fma_rn(delta, av.x, cv.x);
+                    cv.y = __fma_rn(delta, av.y, cv.y);
+                    Cd[j * 32] = cv;
                 }
                 sm.x[row * 32 + lane] += (up > 0 ? -2 : 2);
                 if (((wk.radm1 >> (4 * d)) & 15u) > 1u)
@@ -292,7 +310,7 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem<LMAX>& sm, int
                 const double xv = (double)sm.x[i * 32 + q];
                 double tx = xv * av.x, ty = xv * av.y;
                 if (dg >= 0) {
-                    const double2 cv = sm.C[(dg * LMAX + j) * 32 + q];
+                    const double2 cv = sm.C[(dg * sm.ld + j) * 32 + q];
                     tx -= cv.x;
                     ty -= cv.y;
                 }
@@ -310,10 +328,9 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem<LMAX>& sm, int
         __threadfence();  // every lane's slot entries, before the count
         __syncwarp();
         if (lane == 0) {
-            int old = atomicAdd(a.counters + 1 + t.perm, 1);
+            const int old = atomicAdd(a.counters + 1 + t.perm, 1);
             last = (old == D.ntasks - 1);
         }
-        __syncwarp();
         last = __shfl_sync(0xffffffffu, last, 0);
         if (!last)
             return;
@@ -337,47 +354,37 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem<LMAX>& sm, int
             gx += __ldcg(base_slot + 2 * ((int64_t)q * kl + e));
             gy += __ldcg(base_slot + 2 * ((int64_t)q * kl + e) + 1);
         }
-        if (!D.trivial) {
-            gx = scalbn(gx, 1 - n);
-            gy = scalbn(gy, 1 - n);
-        }
+        gx = scalbn(gx, 1 - D.n);
+        gy = scalbn(gy, 1 - D.n);
         // grad_b = coef * conj(G)
         outg[e] = make_double2(coef.x * gx + coef.y * gy, coef.y * gx - coef.x * gy);
     }
 }
 
-template <int LMAX>
-__global__ void __launch_bounds__(256) glynn_bwd_persistent(BwdArgs a, int kmax, int jb)
+__global__ void __launch_bounds__(256) glynn_bwd_kernel(BwdArgs a, int64_t t_begin,
+                                                         int64_t t_end, int kmax, int ld, int jb,
+                                                         int queue)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    BwdSmem<LMAX> sm(smem_raw + warp * bwd_warp_smem_bytes(kmax, LMAX, jb), kmax, jb);
+    BwdSmem sm(smem_raw + warp * bwd_warp_smem_bytes(kmax, ld, jb), kmax, ld, jb);
     int staged = -1;
-    for (;;) {
-        int ti = 0;
-        if (lane == 0)
-            ti = atomicAdd(a.counters, 1);
-        ti = __shfl_sync(0xffffffffu, ti, 0);
-        if (ti >= a.ntasks)
-            break;
-        Task t = a.tasks[ti];
-        bwd_task<LMAX>(a, t, sm, staged, lane, jb);
-    }
-}
-
-template <int LMAX>
-__global__ void __launch_bounds__(256) glynn_bwd_plain(BwdArgs a, int64_t t_begin, int64_t t_end,
-                                                       int kmax, int jb)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    BwdSmem<LMAX> sm(smem_raw + warp * bwd_warp_smem_bytes(kmax, LMAX, jb), kmax, jb);
-    int staged = -1;
-    int64_t ti = t_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (ti >= t_end)
+    if (!queue) {
+        const int64_t ti = t_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+        if (ti < t_end)
+            bwd_task(a, a.tasks[ti], sm, staged, lane);
         return;
-    Task t = a.tasks[ti];
-    bwd_task<LMAX>(a, t, sm, staged, lane, jb);
+    }
+    for (;;) {
+        int q = 0;
+        if (lane == 0)
+            q = atomicAdd(a.counters, 1);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        const int64_t ti = t_begin + q;
+        if (ti >= t_end)
+            break;
+        bwd_task(a, a.tasks[ti], sm, staged, lane);
+    }
 }
 
 // ---------------------------------------------------------------- scatter
@@ -443,77 +450,46 @@ __global__ void scatter_bs_kernel(const PermDesc* desc, const int32_t* meta, int
 }
 
 // ---------------------------------------------------------------- host side
-int bwd_smem_per_warp(int kmax, int lmax) { return bwd_warp_smem_bytes(kmax, lmax, kMaxLowDigits); }
+int bwd_smem_bytes_for(int kmax, int ld, int jb) { return bwd_warp_smem_bytes(kmax, ld, jb); }
 
-static const int g_bwd_jb = kBwdMaxLowDigits;
-
-template <int LMAX>
-static cudaError_t bwd_attrs(int bytes)
+int bwd_regs_per_thread(int)
 {
-    cudaError_t e = cudaFuncSetAttribute(glynn_bwd_persistent<LMAX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(glynn_bwd_plain<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes);
+    cudaFuncAttributes at{};
+    return cudaFuncGetAttributes(&at, glynn_bwd_kernel) == cudaSuccess ? at.numRegs : 255;
 }
 
-cudaError_t bwd_prepare(int lmax, int smem_bytes)
+cudaError_t bwd_prepare(int, int smem_bytes)
 {
-    switch (lmax) {
-    case 8: return bwd_attrs<8>(smem_bytes);
-    case 16: return bwd_attrs<16>(smem_bytes);
-    case 24: return bwd_attrs<24>(smem_bytes);
-    case 32: return bwd_attrs<32>(smem_bytes);
-    case 40: return bwd_attrs<40>(smem_bytes);
-    default: return cudaErrorInvalidValue;
-    }
+    return cudaFuncSetAttribute(glynn_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_bytes);
 }
 
-int bwd_smem_bytes_for(int kmax, int lmax, int jb) { return bwd_warp_smem_bytes(kmax, lmax, jb); }
-
-cudaError_t bwd_launch_persistent(int lmax, const BwdArgs& a, int kmax, int blocks, int wpb,
+cudaError_t bwd_launch_persistent(int ld, const BwdArgs& a, int kmax, int blocks, int wpb,
                                   cudaStream_t st)
 {
-    const int jb = g_bwd_jb;
-    const int smem = wpb * bwd_warp_smem_bytes(kmax, lmax, jb);
-    const dim3 grid(blocks), block(32 * wpb);
-    switch (lmax) {
-    case 8: glynn_bwd_persistent<8><<<grid, block, smem, st>>>(a, kmax, jb); break;
-    case 16: glynn_bwd_persistent<16><<<grid, block, smem, st>>>(a, kmax, jb); break;
-    case 24: glynn_bwd_persistent<24><<<grid, block, smem, st>>>(a, kmax, jb); break;
-    case 32: glynn_bwd_persistent<32><<<grid, block, smem, st>>>(a, kmax, jb); break;
-    case 40: glynn_bwd_persistent<40><<<grid, block, smem, st>>>(a, kmax, jb); break;
-    default: return cudaErrorInvalidValue;
-    }
+    const int smem = wpb * bwd_warp_smem_bytes(kmax, ld, kBwdMaxLowDigits);
+    glynn_bwd_kernel<<<blocks, 32 * wpb, smem, st>>>(a, 0, a.ntasks, kmax, ld, kBwdMaxLowDigits,
+                                                     1);
     return cudaGetLastError();
 }
 
-cudaError_t bwd_launch_plain(int lmax, const BwdArgs& a, int64_t t_begin, int64_t t_end, int kmax,
+cudaError_t bwd_launch_plain(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end, int kmax,
                              int wpb, cudaStream_t st)
 {
-    const int jb = g_bwd_jb;
-    const int smem = wpb * bwd_warp_smem_bytes(kmax, lmax, jb);
+    const int smem = wpb * bwd_warp_smem_bytes(kmax, ld, kBwdMaxLowDigits);
     const int64_t nt = t_end - t_begin;
-    const dim3 grid((unsigned)((nt + wpb - 1) / wpb)), block(32 * wpb);
-    switch (lmax) {
-    case 8: glynn_bwd_plain<8><<<grid, block, smem, st>>>(a, t_begin, t_end, kmax, jb); break;
-    case 16: glynn_bwd_plain<16><<<grid, block, smem, st>>>(a, t_begin, t_end, kmax, jb); break;
-    case 24: glynn_bwd_plain<24><<<grid, block, smem, st>>>(a, t_begin, t_end, kmax, jb); break;
-    case 32: glynn_bwd_plain<32><<<grid, block, smem, st>>>(a, t_begin, t_end, kmax, jb); break;
-    case 40: glynn_bwd_plain<40><<<grid, block, smem, st>>>(a, t_begin, t_end, kmax, jb); break;
-    default: return cudaErrorInvalidValue;
-    }
+    const unsigned grid = (unsigned)((nt + wpb - 1) / wpb);
+    glynn_bwd_kernel<<<grid, 32 * wpb, smem, st>>>(a, t_begin, t_end, kmax, ld, kBwdMaxLowDigits,
+                                                   0);
     return cudaGetLastError();
 }
 
 cudaError_t scatter_grad_batch(const PermDesc* desc, const int32_t* meta, int64_t nperm,
                                const double2* grad_local, const int64_t* grad_local_off,
                                const int64_t* item_mat_off, const int32_t* item_l,
-                               const int32_t* item_k, double2* grad_mats, int64_t total_elems,
+                               const int32_t* item_k, double2* grad_mats, int64_t,
                                cudaStream_t st)
 {
-    (void)total_elems;
     if (nperm == 0)
         return cudaSuccess;
     scatter_batch_kernel<<<(unsigned)nperm, 128, 0, st>>>(desc, meta, grad_local, grad_local_off,

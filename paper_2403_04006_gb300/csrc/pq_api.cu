@@ -49,38 +49,22 @@ extern "C" const char* pq_last_error(void) { return g_err.c_str(); }
 extern "C" const char* pq_version(void) { return "pq-gb300 0.1 (sm_103a)"; }
 
 // ---------------------------------------------------------------- tuning table
-// Process-wide chunk length (log2) per (product-column class, photon number),
-// filled by pq_autotune and read by later plans.
+// Process-wide chunk length (log2) per photon number (size class), filled by
+// pq_autotune and read by later plans.
 static std::mutex g_tune_mu;
-static int g_tune[5][PQ_MAX_N + 1];
-static bool g_tune_init = false;
+static int g_tune[PQ_MAX_N + 1] = {0};
 
-static int tune_get(int lclass, int n)
+static int tune_get(int n)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (!g_tune_init) {
-        for (auto& row : g_tune)
-            for (int& v : row)
-                v = 0;
-        g_tune_init = true;
-    }
-    int ci = 0;
-    while (ci < 5 && kLmaxClasses[ci] != lclass)
-        ++ci;
-    if (ci == 5 || n < 0 || n > PQ_MAX_N)
-        return 0;
-    return g_tune[ci][n];
+    return (n < 0 || n > PQ_MAX_N) ? 0 : g_tune[n];
 }
 
-static void tune_set(int lclass, int n, int v)
+static void tune_set(int n, int v)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    int ci = 0;
-    while (ci < 5 && kLmaxClasses[ci] != lclass)
-        ++ci;
-    if (ci == 5 || n < 0 || n > PQ_MAX_N)
-        return;
-    g_tune[ci][n] = v;
+    if (n >= 0 && n <= PQ_MAX_N)
+        g_tune[n] = v;
 }
 
 // ---------------------------------------------------------------- planning
@@ -174,6 +158,30 @@ static int build_item(const int32_t* r, const int32_t* c, int k0, int l0, int64_
     if (it.l > PQ_MAX_PRODUCT_COLS)
         return fail(PQ_ERR_UNSUPPORTED, "%d product-side columns above %d", it.l,
                     PQ_MAX_PRODUCT_COLS);
+    // product columns by non-increasing multiplicity; extra prefix factors:
+    // prod_j S_j^{c_j} = prod_{m>=1} P(n_m), n_m = #{j : c_j >= m}, and P(j+1)
+    // appears c_j - max(c_{j+1}, 1) extra times (c_l = 0)
+    {
+        std::vector<int> ord(it.l);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int a, int b) { return it.cmul[a] > it.cmul[b]; });
+        std::vector<int32_t> ci(it.l), cm2(it.l);
+        for (int j = 0; j < it.l; ++j) {
+            ci[j] = it.cidx[ord[j]];
+            cm2[j] = it.cmul[ord[j]];
+        }
+        it.cidx = ci;
+        it.cmul = cm2;
+        it.ecnt.assign(it.l, 0);
+        it.jf = -1;
+        for (int j = 0; j < it.l; ++j) {
+            const int next = (j + 1 < it.l) ? it.cmul[j + 1] : 0;
+            it.ecnt[j] = std::max(0, it.cmul[j] - std::max(next, 1));
+            if (it.ecnt[j] > 0 && it.jf < 0)
+                it.jf = j;
+        }
+    }
     // digits: fixed copy on the least repeated row, ascending radix
     int f = (int)(std::min_element(it.rmul.begin(), it.rmul.end()) - it.rmul.begin());
     struct Dg {
@@ -246,7 +254,7 @@ static int default_log2_for(const pq_plan* P, const ItemPlan& it)
         return P->opts.chunk_log2;
     if (it.n >= 0 && it.n < (int)P->class_log2.size() && P->class_log2[it.n] > 0)
         return P->class_log2[it.n];
-    int tuned = tune_get(P->lmax, it.n);
+    int tuned = tune_get(it.n);
     if (tuned > 0)
         return tuned;
     return 10;
@@ -315,9 +323,7 @@ static int schedule_and_upload(pq_plan* P)
         lmax_needed = std::max(lmax_needed, it.l);
         kmax = std::max(kmax, it.k);
     }
-    P->lmax = lmax_class(lmax_needed);
-    if (P->lmax < 0)
-        return fail(PQ_ERR_UNSUPPORTED, "product side of %d columns", lmax_needed);
+    P->lmax = lmax_needed;
     P->kmax = kmax;
     for (ItemPlan& it : P->items)
         choose_chunks(it, default_log2_for(P, it));
@@ -347,6 +353,7 @@ static int schedule_and_upload(pq_plan* P)
         D.weighted = it.weighted ? 1 : 0;
         D.out = (int32_t)p;
         D.trivial = it.trivial ? 1 : 0;
+        D.jf = it.jf;
         D.L = it.L;
         D.norm = it.norm;
         auto app = [&](const std::vector<int32_t>& v) {
@@ -359,6 +366,7 @@ static int schedule_and_upload(pq_plan* P)
         app(it.drow);
         app(it.drad);
         app(it.dtop);
+        app(it.ecnt);
         int64_t nt = it.trivial ? 1 : (it.nchunks + kWarp - 1) / kWarp;
         if (nt > (int64_t(1) << 30))
             return fail(PQ_ERR_UNSUPPORTED, "too many tasks for one permanent");
@@ -394,14 +402,14 @@ static int schedule_and_upload(pq_plan* P)
         P->tasks_batched_h[q] = P->tasks_plain_h[order[q]];
 
     // launch geometry
-    int wpb = P->opts.warps_per_block > 0 ? P->opts.warps_per_block : 8;
     const int per_warp = fwd_smem_per_warp(P->kmax, P->lmax);
-    while (wpb > 1 && wpb * per_warp > 200 * 1024)
-        --wpb;
     if (per_warp > 200 * 1024)
         return fail(PQ_ERR_UNSUPPORTED, "shared memory per warp %d too large", per_warp);
+    int wpb = 0, bps = 0;
+    launch_geometry(fwd_regs_per_thread(P->lmax), per_warp,
+                    P->opts.warps_per_block > 0 ? P->opts.warps_per_block : 8,
+                    P->opts.blocks_per_sm > 0 ? P->opts.blocks_per_sm : 8, wpb, bps);
     P->wpb = wpb;
-    int bps = P->opts.blocks_per_sm > 0 ? P->opts.blocks_per_sm : 1;
     P->blocks = std::max(1, P->num_sms * bps);
 
     P->stats.permanents = np;
@@ -844,7 +852,7 @@ static int ensure_backward(pq_plan* P)
     int64_t gpart = 0, gl = 0;
     for (int64_t p = 0; p < np; ++p) {
         ItemPlan& it = items[p];
-        choose_chunks(it, 5, kBwdMaxLowDigits);
+        choose_chunks(it, kBwdChunkLog2, kBwdMaxLowDigits);
         PermDesc& D = P->desc_bwd_h[p];
         D.J = it.J;
         D.L = it.L;
@@ -900,13 +908,13 @@ static int ensure_backward(pq_plan* P)
         if ((rc = dev_upload(&P->item_l_d, P->item_l)) != PQ_OK)
             return rc;
     }
-    int wpb = 4;
     const int per_warp = bwd_smem_bytes_for(P->kmax, P->lmax, kBwdMaxLowDigits);
-    while (wpb > 1 && wpb * per_warp > 200 * 1024)
-        --wpb;
     if (per_warp > 200 * 1024)
         return fail(PQ_ERR_UNSUPPORTED, "backward shared memory per warp %d too large", per_warp);
+    int wpb = 0, bps = 0;
+    launch_geometry(bwd_regs_per_thread(P->lmax), per_warp, 4, 8, wpb, bps);
     P->bwd_wpb = wpb;
+    P->bwd_blocks = std::max(1, P->num_sms * bps);
     cudaError_t e = bwd_prepare(P->lmax, wpb * per_warp);
     if (e != cudaSuccess)
         return fail(PQ_ERR_CUDA, "backward attribute setup failed: %s", cudaGetErrorString(e));
@@ -948,7 +956,7 @@ static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, co
         }
     } else {
         a.tasks = P->tasks_bwd_batched_d;
-        e = bwd_launch_persistent(P->lmax, a, P->kmax, P->blocks, P->bwd_wpb, st);
+        e = bwd_launch_persistent(P->lmax, a, P->kmax, P->bwd_blocks, P->bwd_wpb, st);
         if (e != cudaSuccess)
             return fail(PQ_ERR_CUDA, "backward launch failed: %s", cudaGetErrorString(e));
     }
@@ -1146,7 +1154,7 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
             }
         }
         P->class_log2[n] = best_c;
-        tune_set(P->lmax, n, best_c);
+        tune_set(n, best_c);
     }
     P->opts.chunk_log2 = saved_opt;
     if (rc == PQ_OK)

@@ -140,6 +140,7 @@ struct MetaView {
     const int32_t* drow;
     const int32_t* drad;
     const int32_t* dtop;
+    const int32_t* ecnt;
 };
 
 __device__ __forceinline__ MetaView meta_view(const int32_t* pool, const PermDesc& D)
@@ -152,6 +153,7 @@ __device__ __forceinline__ MetaView meta_view(const int32_t* pool, const PermDes
     m.drow = m.cmul + D.l;
     m.drad = m.drow + D.ndig;
     m.dtop = m.drad + D.ndig;
+    m.ecnt = m.dtop + D.ndig;
     return m;
 }
 

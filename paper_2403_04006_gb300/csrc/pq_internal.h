@@ -46,7 +46,7 @@ struct alignas(16) PermDesc {
     int32_t ntasks;   // warp tasks of this permanent
     int32_t out;      // output index
     int32_t trivial;  // 1: n == 0, per = 1
-    int32_t pad;
+    int32_t jf;       // first product column whose prefix is an extra factor (-1: none)
     int64_t L;        // chunk length
     double norm;      // 1 / (prod t! prod s!) for boson sampling, else 1
     double pad2;
@@ -58,7 +58,13 @@ struct alignas(16) PermDesc {
 //   rmul[k]  row multiplicities (summed side)
 //   cmul[l]  column multiplicities (product side)
 //   drow[ndig] row of digit d; drad[ndig] radix of digit d; dtop[ndig] binomial top
-inline int meta_size(int k, int l, int ndig) { return 2 * k + 2 * l + 3 * ndig; }
+//   ecnt[l]  extra factors at product column j (see below)
+// Product columns are sorted by non-increasing multiplicity c_0 >= c_1 >= ...
+// Then prod_j S_j^{c_j} = prod_{m >= 1} P(n_m), with P(q) = S_0 ... S_{q-1} and
+// n_m the number of columns with c_j >= m, so a term needs l - 1 products for
+// P(l) plus one product per extra prefix: ecnt[j] = c_j - max(c_{j+1}, 1)
+// (c_l = 0) extra copies of P(j + 1).
+inline int meta_size(int k, int l, int ndig) { return 2 * k + 3 * l + 3 * ndig; }
 
 struct alignas(8) Task {
     int32_t perm;  // permanent

@@ -6,19 +6,31 @@
 
 namespace pqi {
 
-// Product-side column bound classes the kernels are compiled for.
-constexpr int kLmaxClasses[] = {8, 16, 24, 32, 40};
-
-inline int lmax_class(int l)
-{
-    for (int c : kLmaxClasses)
-        if (l <= c)
-            return c;
-    return -1;
-}
-
 // ---- forward (glynn_fwd.cu)
 int fwd_smem_per_warp(int kmax, int lmax);
+int fwd_regs_per_thread(int lmax);
+int bwd_regs_per_thread(int lmax);
+
+// Warps per block and resident blocks per SM that registers and shared
+// memory allow (65536 registers per SM, allocated per warp in units of 256;
+// up to 227 KB of shared memory per SM for all resident blocks).
+inline void launch_geometry(int regs_per_thread, int smem_per_warp, int want_wpb,
+                            int want_bps, int& wpb, int& bps)
+{
+    const int regs_warp = ((regs_per_thread * 32 + 255) / 256) * 256;
+    int max_warps = 65536 / regs_warp;
+    if (max_warps < 1)
+        max_warps = 1;
+    wpb = want_wpb < max_warps ? want_wpb : max_warps;
+    while (wpb > 1 && wpb * smem_per_warp > 220 * 1024)
+        --wpb;
+    int by_regs = max_warps / wpb;
+    int by_smem = smem_per_warp > 0 ? (227 * 1024) / (wpb * smem_per_warp) : 32;
+    int cap = by_regs < by_smem ? by_regs : by_smem;
+    if (cap < 1)
+        cap = 1;
+    bps = want_bps < cap ? want_bps : cap;
+}
 cudaError_t fwd_prepare(int lmax, int smem_bytes);
 cudaError_t fwd_launch_persistent(int lmax, const ExecArgs& a, int kmax, int blocks, int wpb,
                                   cudaStream_t st);
@@ -44,7 +56,8 @@ struct BwdArgs {
 };
 int bwd_smem_per_warp(int kmax, int lmax);
 int bwd_smem_bytes_for(int kmax, int lmax, int jb);
-constexpr int kBwdMaxLowDigits = 6;  // low digits the backward workspace holds
+constexpr int kBwdMaxLowDigits = 4;  // low digits the backward workspace holds
+constexpr int kBwdChunkLog2 = 4;     // backward chunks of at most 2^4 terms
 cudaError_t bwd_prepare(int lmax, int smem_bytes);
 cudaError_t bwd_launch_persistent(int lmax, const BwdArgs& a, int kmax, int blocks, int wpb,
                                   cudaStream_t st);

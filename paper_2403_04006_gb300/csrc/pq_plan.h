@@ -18,6 +18,8 @@ struct ItemPlan {
     bool transposed = false;
     std::vector<int32_t> ridx, cidx, rmul, cmul;  // oriented
     std::vector<int32_t> drow, drad, dtop;        // digits, ascending radix
+    std::vector<int32_t> ecnt;                    // extra prefix factors per product column
+    int32_t jf = -1;                              // first column with an extra (-1: unit)
     int32_t J = 0;
     int64_t T = 0, L = 1, nchunks = 0;
     bool weighted = false;
@@ -43,6 +45,7 @@ struct pq_plan {
     int wpb = 8;
     int blocks = 0;
     int bwd_wpb = 4;
+    int bwd_blocks = 0;
     int bwd_kmax = 1;
     // boson sampling inputs
     int32_t m = 0;
