@@ -458,8 +458,15 @@ int bwd_regs_per_thread(int)
     return cudaFuncGetAttributes(&at, glynn_bwd_kernel) == cudaSuccess ? at.numRegs : 255;
 }
 
+// Raise (never lower) the kernel's dynamic shared-memory limit.
 cudaError_t bwd_prepare(int, int smem_bytes)
 {
+    cudaFuncAttributes at{};
+    cudaError_t e = cudaFuncGetAttributes(&at, glynn_bwd_kernel);
+    if (e != cudaSuccess)
+        return e;
+    if (at.maxDynamicSharedSizeBytes >= smem_bytes)
+        return cudaSuccess;
     return cudaFuncSetAttribute(glynn_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_bytes);
 }

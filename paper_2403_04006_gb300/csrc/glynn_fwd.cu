@@ -344,8 +344,16 @@ int fwd_regs_per_thread(int)
     return cudaFuncGetAttributes(&at, glynn_fwd_kernel) == cudaSuccess ? at.numRegs : 255;
 }
 
+// Raise (never lower) the kernel's dynamic shared-memory limit: plans made
+// earlier with larger workspaces must keep launching.
 cudaError_t fwd_prepare(int, int smem_bytes)
 {
+    cudaFuncAttributes at{};
+    cudaError_t e = cudaFuncGetAttributes(&at, glynn_fwd_kernel);
+    if (e != cudaSuccess)
+        return e;
+    if (at.maxDynamicSharedSizeBytes >= smem_bytes)
+        return cudaSuccess;
     return cudaFuncSetAttribute(glynn_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_bytes);
 }

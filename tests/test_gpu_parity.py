@@ -364,3 +364,18 @@ def test_bs_backward_plain_matches_batched(dev):
 def test_fp64_probe_runs(dev):
     flops, ms = api.probe_fp64_peak(1 << 12)
     assert flops > 1e11 and ms > 0
+
+
+def test_later_plan_with_smaller_workspace_keeps_earlier_plan_working(dev):
+    """A plan made later with less shared memory per block must not lower the
+    launch limit an earlier, larger plan relies on."""
+    A = W.single_large(26)
+    big = W.pack_batch([(A, [1] * 26, [1] * 26)])
+    ref = O.perm_ryser(A, gold=True, nthreads=O.default_threads())
+    db = api.DeviceBatch(big, dev)
+    plan_big = api.Plan.for_batch(big)
+    small = W.pack_batch([(np.array([[0.5 + 0.5j]]), [1], [1])])
+    plan_small = api.Plan.for_batch(small)
+    api.permanent_batched(api.DeviceBatch(small, dev), plan_small)
+    got = api.permanent_batched(db, plan_big).cpu().numpy()
+    assert rel_err(got[0], ref) <= TOL
