@@ -221,6 +221,35 @@ int pq_plan_get_stats(const pq_plan* plan, pq_plan_stats* out);
  * the paper's method; it provides the roofline denominator. */
 int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms, void* stream);
 
+/* ---- Permanent without allocation ---------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: code running while a stream is captured
+ * into a CUDA graph (where cudaMalloc is not allowed), code inside a
+ * framework whose caching allocator owns the device memory, and
+ * latency-critical paths that cannot pay for the device synchronisation an
+ * allocation may cause.
+ *
+ * Computes per(A) of ONE base matrix exactly like pq_permanent_batched (same
+ * kernel, same method) but allocates nothing: the descriptor, the task list,
+ * the partial sums and the counters live in a static device array of
+ * PQ_NOALLOC_SCRATCH_BYTES that every GPU holds from the moment it loads the
+ * library until the process exits.
+ *   B: device, k x l row-major complex; row_mult[k], col_mult[l]: HOST
+ *   (read during the call); out: device, one complex.  Asynchronous on stream.
+ * Errors: PQ_ERR_ARG (null, negative, sum r != sum c); PQ_ERR_UNSUPPORTED
+ * beyond the limits of pq.h or when the permanent needs more warp tasks
+ * than the array holds (about 26,000 tasks: every collision-free permanent up
+ * to n = 35 fits);
+ * PQ_ERR_CUDA.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call reuses the same array (the counters are cleared at the start of each
+ * call), so calls whose GPU work overlaps -- on two streams or from two host
+ * threads -- race with each other: serialise them. */
+#define PQ_NOALLOC_SCRATCH_BYTES (1 << 20)
+int pq_permanent_noalloc(const pq_c128* B, int32_t k, int32_t l, const int32_t* row_mult,
+                         const int32_t* col_mult, pq_c128* out, void* stream);
+
 /* ---- Diagnostics (host only; no GPU needed) ---------------------------- */
 
 /* How the planner treats one permanent: the side it sums, the digits of the

@@ -46,6 +46,10 @@ static int fail(int code, const char* fmt, ...)
     } while (0)
 
 extern "C" const char* pq_last_error(void) { return g_err.c_str(); }
+
+namespace pqi {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace pqi
 extern "C" const char* pq_version(void) { return "pq-gb300 0.1 (sm_103a)"; }
 
 // ---------------------------------------------------------------- tuning table

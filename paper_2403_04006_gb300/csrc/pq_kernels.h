@@ -80,6 +80,9 @@ cudaError_t clements_forward(const double* theta, const double* phi, int m, doub
 cudaError_t clements_backward(const double* theta, const double* phi, int m, const double2* U,
                               const double2* gU, double* gtheta, double* gphi, cudaStream_t st);
 
+// ---- error message of the calling thread, read by pq_last_error (pq_api.cu)
+void set_last_error(const char* msg);
+
 // ---- FP64 probe (fp64_probe.cu)
 cudaError_t fp64_probe(int64_t iters, double* flops_per_s, double* ms, cudaStream_t st);
 

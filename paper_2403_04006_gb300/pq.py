@@ -71,6 +71,7 @@ _SIGNATURES = {
     "pq_plan_get_stats": (_i32, [_vp, ctypes.POINTER(pq_plan_stats)]),
     "pq_probe_fp64_peak": (_i32, [_i64, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double), _vp]),
+    "pq_permanent_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp]),
     "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "pq_last_error": (ctypes.c_char_p, []),
@@ -185,6 +186,18 @@ def pq_probe_fp64_peak(iters: int, stream=None) -> tuple[float, float]:
     _check(load_library().pq_probe_fp64_peak(iters, ctypes.byref(f), ctypes.byref(ms), stream),
            "pq_probe_fp64_peak")
     return f.value, ms.value
+
+
+def pq_permanent_noalloc(B_ptr, k: int, l: int, row_mult: np.ndarray, col_mult: np.ndarray,
+                         out_ptr, stream):
+    """Permanent of one base matrix with no device allocation (static device
+    workspace shared by all calls; serialise calls).  row_mult / col_mult are
+    host int32 arrays."""
+    r = np.ascontiguousarray(row_mult, dtype=np.int32)
+    c = np.ascontiguousarray(col_mult, dtype=np.int32)
+    _check(load_library().pq_permanent_noalloc(B_ptr, k, l, r.ctypes.data if r.size else None,
+                                               c.ctypes.data if c.size else None, out_ptr,
+                                               stream), "pq_permanent_noalloc")
 
 
 def pq_version() -> str:
