@@ -200,8 +200,12 @@ int pq_clements_backward(const double* theta, const double* phi, int32_t m, cons
 int pq_autotune(pq_plan* plan, const pq_batch* b, const pq_c128* U, void* stream);
 
 /* Statistics of a plan, host memory: number of permanents, total Gray-code
- * terms, algorithmic FP64 flops of one forward execution (FMA = 2), number of
- * warp tasks and of kernel launches one execution makes. */
+ * terms, algorithmic FP64 flops of one forward execution (FMA = 2; the count
+ * of a straightforward Glynn evaluation: 2l + 6(n-1) + 2 per term, +2 for a
+ * non-unit weight), FP64 instructions the forward kernel needs for its terms
+ * (Gray step, products, fused accumulation, weights, double-double fold;
+ * each DADD, DMUL or DFMA counts one), number of warp tasks and of kernel
+ * launches one execution makes. */
 typedef struct {
     int64_t permanents;
     int64_t terms;
@@ -212,6 +216,7 @@ typedef struct {
     int64_t launches_backward;
     int32_t lmax;
     int32_t reserved;
+    double fp64_instr_forward;
 } pq_plan_stats;
 int pq_plan_get_stats(const pq_plan* plan, pq_plan_stats* out);
 

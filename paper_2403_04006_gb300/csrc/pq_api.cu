@@ -247,6 +247,20 @@ static double fwd_flops_per_term(const ItemPlan& it)
     return 2.0 * it.l + 6.0 * (it.n - 1) + 2.0 + (it.weighted ? 2.0 : 0.0);
 }
 
+// FP64 instructions of one term in glynn_fwd.cu: Gray step 2l; products of
+// P(l) and the extra prefixes, 4 each; fused accumulation 4; weight 2; the
+// double-double fold, 14 every 16 terms.
+static double fwd_instr_per_term(const ItemPlan& it)
+{
+    if (it.n == 1)
+        return 2.0;
+    int cmax = 1;
+    for (int c : it.cmul)
+        cmax = std::max(cmax, c);
+    const double products = (cmax == 1) ? (it.l - 2) : (it.l + cmax - 3);
+    return 2.0 * it.l + 4.0 * products + 4.0 + (it.weighted ? 2.0 : 0.0) + 14.0 / 16.0;
+}
+
 static double bwd_flops_per_term(const ItemPlan& it)
 {
     return fwd_flops_per_term(it) + 18.0 * it.l + 8.0 * it.k * it.l;
@@ -338,7 +352,7 @@ static int schedule_and_upload(pq_plan* P)
     P->plain_first.assign(np + 1, 0);
     std::vector<double> task_cost;
     int32_t slot = 0;
-    double flops_f = 0.0, flops_b = 0.0;
+    double flops_f = 0.0, flops_b = 0.0, instr_f = 0.0;
     int64_t terms = 0;
     for (int64_t p = 0; p < np; ++p) {
         ItemPlan& it = P->items[p];
@@ -390,6 +404,7 @@ static int schedule_and_upload(pq_plan* P)
         if (!it.trivial) {
             terms += it.T;
             flops_f += (double)it.T * fpt;
+            instr_f += (double)it.T * fwd_instr_per_term(it);
             flops_b += (double)it.T * bwd_flops_per_term(it);
         }
         if (slot < 0)
@@ -420,6 +435,7 @@ static int schedule_and_upload(pq_plan* P)
     P->stats.terms = terms;
     P->stats.flops_forward = flops_f;
     P->stats.flops_backward = flops_b;
+    P->stats.fp64_instr_forward = instr_f;
     P->stats.tasks = (int64_t)P->tasks_plain_h.size();
     P->stats.launches_forward = (P->opts.method == PQ_METHOD_PLAIN) ? np : 1;
     P->stats.launches_backward = (P->opts.method == PQ_METHOD_PLAIN) ? np + 1 : 2;
