@@ -32,10 +32,12 @@
 
 namespace pqi {
 
-// Per-warp shared memory (ld = product-column bound, jb = low-digit bound).
-__host__ __device__ inline int bwd_warp_smem_bytes(int kmax, int ld, int jb)
+// Per-warp shared memory: ld = product-column bound, jb = low digits of the
+// plan's chunks, n2 = repeated product columns at most (powers are kept only
+// for those).
+__host__ __device__ inline int bwd_warp_smem_bytes(int kmax, int ld, int jb, int n2)
 {
-    long bytes = 16L * (kmax * ld + ld + 5L * 32 * ld + 32L * jb * ld) + 8L * 32 +
+    long bytes = 16L * (kmax * ld + ld + 3L * 32 * ld + 2L * 32 * n2 + 32L * jb * ld) + 8L * 32 +
                  4L * (32L * kmax + 16 + ld + kmax);
     return (int)((bytes + 15) & ~15L);
 }
@@ -46,8 +48,8 @@ struct BwdSmem {
     double2* S;       // ld x 32 (lane-major)
     double2* A;       // ld x 32
     double2* P;       // ld x 32
-    double2* PW;      // ld x 32
-    double2* FULL;    // ld x 32
+    double2* PW;      // n2 x 32
+    double2* FULL;    // n2 x 32
     double2* C;       // jb x ld x 32
     double* wh;       // 32
     int32_t* x;       // kmax x 32
@@ -55,7 +57,7 @@ struct BwdSmem {
     int32_t* cm;      // ld
     int32_t* rowdig;  // kmax: low digit of each row, or -1
     int ld;
-    __device__ BwdSmem(unsigned char* raw, int kmax, int ld_, int jb)
+    __device__ BwdSmem(unsigned char* raw, int kmax, int ld_, int jb, int n2)
     {
         ld = ld_;
         M = reinterpret_cast<double2*>(raw);
@@ -64,8 +66,8 @@ struct BwdSmem {
         A = S + 32 * ld;
         P = A + 32 * ld;
         PW = P + 32 * ld;
-        FULL = PW + 32 * ld;
-        C = FULL + 32 * ld;
+        FULL = PW + 32 * n2;
+        C = FULL + 32 * n2;
         wh = reinterpret_cast<double*>(C + 32 * jb * ld);
         x = reinterpret_cast<int32_t*>(wh + 32);
         lowrow = x + kmax * 32;
@@ -363,11 +365,11 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
 
 __global__ void __launch_bounds__(256) glynn_bwd_kernel(BwdArgs a, int64_t t_begin,
                                                          int64_t t_end, int kmax, int ld, int jb,
-                                                         int queue)
+                                                         int n2, int queue)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    BwdSmem sm(smem_raw + warp * bwd_warp_smem_bytes(kmax, ld, jb), kmax, ld, jb);
+    BwdSmem sm(smem_raw + warp * bwd_warp_smem_bytes(kmax, ld, jb, n2), kmax, ld, jb, n2);
     int staged = -1;
     if (!queue) {
         const int64_t ti = t_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -415,33 +417,25 @@ __global__ void scatter_batch_kernel(const PermDesc* desc, const int32_t* meta,
 }
 
 // Boson sampling: grad_U[a][c] = sum over patterns (in order) of the entry of
-// that pattern's gradient that U[a][c] became.
-__global__ void scatter_bs_kernel(const PermDesc* desc, const int32_t* meta, int64_t nperm, int m,
+// that pattern's gradient that U[a][c] became.  pos[p][2m] maps output mode a
+// and input mode c to the oriented (row, column) indices of pattern p's base
+// matrix: pos[p][a] = row of a, pos[p][m + c] = column of c, -1 if absent
+// (for a pattern whose summed side is its input modes the roles swap in the
+// planner, which writes the map accordingly).
+__global__ void scatter_bs_kernel(const PermDesc* desc, int64_t nperm, int m, const int32_t* pos,
                                   const double2* gl, const int64_t* gl_off, double2* gU)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
         const int ar = e / m, ac = e - ar * m;  // U row (output mode), column (input mode)
         double gx = 0.0, gy = 0.0;
         for (int64_t p = 0; p < nperm; ++p) {
-            const PermDesc D = desc[p];
-            if (D.trivial)
+            const int32_t* pp = pos + p * 2 * (int64_t)m;
+            const int io = pp[ar], jo = pp[m + ac];
+            if (io < 0 || jo < 0)
                 continue;
-            const MetaView mv = meta_view(meta, D);
-            // source element (ar, ac) sits at ar * m + ac = ridx*si + cidx*sj
-            int io = -1, jo = -1;
-            const int want_i = (D.si == 1) ? ac : ar;  // transposed: summed side is columns
-            const int want_j = (D.si == 1) ? ar : ac;
-            for (int i = 0; i < D.k; ++i)
-                if (mv.ridx[i] == want_i)
-                    io = i;
-            if (io < 0)
-                continue;
-            for (int j = 0; j < D.l; ++j)
-                if (mv.cidx[j] == want_j)
-                    jo = j;
-            if (jo < 0)
-                continue;
-            const double2 v = gl[gl_off[p] + io * D.l + jo];
+            const int l = desc[p].l;
+            const bool tr = desc[p].si == 1 && m > 1;  // summed side = input modes
+            const double2 v = gl[gl_off[p] + (tr ? (int64_t)jo * l + io : (int64_t)io * l + jo)];
             gx += v.x;
             gy += v.y;
         }
@@ -450,7 +444,10 @@ __global__ void scatter_bs_kernel(const PermDesc* desc, const int32_t* meta, int
 }
 
 // ---------------------------------------------------------------- host side
-int bwd_smem_bytes_for(int kmax, int ld, int jb) { return bwd_warp_smem_bytes(kmax, ld, jb); }
+int bwd_smem_bytes_for(int kmax, int ld, int jb, int n2)
+{
+    return bwd_warp_smem_bytes(kmax, ld, jb, n2);
+}
 
 int bwd_regs_per_thread(int)
 {
@@ -471,23 +468,21 @@ cudaError_t bwd_prepare(int, int smem_bytes)
                                 smem_bytes);
 }
 
-cudaError_t bwd_launch_persistent(int ld, const BwdArgs& a, int kmax, int blocks, int wpb,
-                                  cudaStream_t st)
+cudaError_t bwd_launch_persistent(int ld, const BwdArgs& a, int kmax, int jb, int n2, int blocks,
+                                  int wpb, cudaStream_t st)
 {
-    const int smem = wpb * bwd_warp_smem_bytes(kmax, ld, kBwdMaxLowDigits);
-    glynn_bwd_kernel<<<blocks, 32 * wpb, smem, st>>>(a, 0, a.ntasks, kmax, ld, kBwdMaxLowDigits,
-                                                     1);
+    const int smem = wpb * bwd_warp_smem_bytes(kmax, ld, jb, n2);
+    glynn_bwd_kernel<<<blocks, 32 * wpb, smem, st>>>(a, 0, a.ntasks, kmax, ld, jb, n2, 1);
     return cudaGetLastError();
 }
 
 cudaError_t bwd_launch_plain(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end, int kmax,
-                             int wpb, cudaStream_t st)
+                             int jb, int n2, int wpb, cudaStream_t st)
 {
-    const int smem = wpb * bwd_warp_smem_bytes(kmax, ld, kBwdMaxLowDigits);
+    const int smem = wpb * bwd_warp_smem_bytes(kmax, ld, jb, n2);
     const int64_t nt = t_end - t_begin;
     const unsigned grid = (unsigned)((nt + wpb - 1) / wpb);
-    glynn_bwd_kernel<<<grid, 32 * wpb, smem, st>>>(a, t_begin, t_end, kmax, ld, kBwdMaxLowDigits,
-                                                   0);
+    glynn_bwd_kernel<<<grid, 32 * wpb, smem, st>>>(a, t_begin, t_end, kmax, ld, jb, n2, 0);
     return cudaGetLastError();
 }
 
@@ -504,13 +499,13 @@ cudaError_t scatter_grad_batch(const PermDesc* desc, const int32_t* meta, int64_
     return cudaGetLastError();
 }
 
-cudaError_t scatter_grad_bs(const PermDesc* desc, const int32_t* meta, int64_t nperm, int32_t m,
+cudaError_t scatter_grad_bs(const PermDesc* desc, const int32_t* pos, int64_t nperm, int32_t m,
                             const double2* grad_local, const int64_t* grad_local_off,
                             double2* grad_U, cudaStream_t st)
 {
-    const int threads = 128;
+    const int threads = 64;
     const int blocks = (m * m + threads - 1) / threads;
-    scatter_bs_kernel<<<blocks, threads, 0, st>>>(desc, meta, nperm, m, grad_local, grad_local_off,
+    scatter_bs_kernel<<<blocks, threads, 0, st>>>(desc, nperm, m, pos, grad_local, grad_local_off,
                                                   grad_U);
     return cudaGetLastError();
 }

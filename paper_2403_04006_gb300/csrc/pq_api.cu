@@ -211,7 +211,8 @@ static int build_item(const int32_t* r, const int32_t* c, int k0, int l0, int64_
 
 // Cut the item's code into chunks of the lowest digits: the longest prefix of
 // digits whose radix product stays within the target length.
-static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits)
+static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
+                          int64_t min_chunks = kWarp)
 {
     if (it.trivial) {
         it.J = 0;
@@ -219,7 +220,7 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits)
         it.nchunks = 0;
         return;
     }
-    int64_t target = it.T / kWarp;  // aim for at least one full warp of chunks
+    int64_t target = it.T / min_chunks;  // aim for at least min_chunks chunks
     int64_t cap = int64_t(1) << std::max(0, std::min(log2_cap, 30));
     if (target > cap)
         target = cap;
@@ -231,6 +232,47 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits)
            L * it.drad[J] <= target) {
         L *= it.drad[J];
         ++J;
+    }
+    if (min_chunks == kWarp) {
+        // Batched method: among the neighbouring cuts (one digit longer, up
+        // to two shorter) take the one with the fewest FP64 warp instructions:
+        // every lane of a task executes L terms whether or not it has a chunk,
+        // and every task pays its chunk start-up and reductions.
+        int cmax = 1;
+        for (int c : it.cmul)
+            cmax = std::max(cmax, c);
+        const int nd = (int)it.drad.size();
+        auto cost_of = [&](int j, int64_t lj) {
+            bool w = false;
+            for (int d = 0; d < j; ++d)
+                w = w || it.drad[d] > 2;
+            const double products = (cmax == 1) ? (it.l - 2) : (it.l + cmax - 3);
+            const double ppt = 2.0 * it.l + 4.0 * std::max(products, 0.0) + 4.0 + (w ? 2.0 : 0.0);
+            const double ovh = (nd - j) * (2.0 * it.l + 2.0) + 150.0 + 2.0 * it.k;
+            const int64_t tasks = (it.T / lj + kWarp - 1) / kWarp;
+            return tasks * ((double)lj * ppt + ovh);
+        };
+        int bestJ = J;
+        int64_t bestL = L;
+        double best = cost_of(J, L);
+        int64_t lj = 1;
+        for (int j = 0; j <= J + 1 && j <= nd && j <= jmax; ++j) {
+            if (j > 0) {
+                if (it.drad[j - 1] > kMaxLowRadix)
+                    break;
+                lj *= it.drad[j - 1];
+            }
+            if (j < J - 2 || (j == J + 1 && lj > cap))
+                continue;
+            const double c = cost_of(j, lj);
+            if (c < best * 0.999) {
+                best = c;
+                bestJ = j;
+                bestL = lj;
+            }
+        }
+        J = bestJ;
+        L = bestL;
     }
     it.J = J;
     it.L = L;
@@ -302,7 +344,7 @@ static void free_plan_device(pq_plan* P)
     void* ptrs[] = {P->desc_d,        P->meta_d,           P->tasks_batched_d, P->tasks_plain_d,
                     P->partials_d,    P->counters_d,       P->err_d,           P->gpart_d,
                     P->gpart_off_d,   P->grad_local_d,     P->grad_local_off_d, P->item_mat_off_d,
-                    P->item_k_d,      P->item_l_d,         P->grad_out_tmp_d};
+                    P->item_k_d,      P->item_l_d,         P->grad_out_tmp_d, P->bs_pos_d};
     for (void* p : ptrs)
         if (p)
             cudaFree(p);
@@ -325,6 +367,7 @@ static void free_plan_device(pq_plan* P)
     P->item_mat_off_d = nullptr;
     P->item_k_d = P->item_l_d = nullptr;
     P->grad_out_tmp_d = nullptr;
+    P->bs_pos_d = nullptr;
     if (P->graph) {
         cudaGraphExecDestroy(P->graph);
         P->graph = nullptr;
@@ -343,8 +386,16 @@ static int schedule_and_upload(pq_plan* P)
     }
     P->lmax = lmax_needed;
     P->kmax = kmax;
+    // The plain method runs one permanent per launch, so each permanent is cut
+    // finely enough to occupy the whole GPU (about 4 warps per SM); the batched
+    // method keeps a warp's worth of chunks per permanent and fills the GPU
+    // with many permanents at once.
+    const int64_t plain_chunks = (int64_t)P->num_sms * 4 * kWarp;
     for (ItemPlan& it : P->items)
-        choose_chunks(it, default_log2_for(P, it));
+        choose_chunks(it, default_log2_for(P, it), kMaxLowDigits,
+                      (P->opts.method == PQ_METHOD_PLAIN && P->opts.chunk_log2 == 0)
+                          ? plain_chunks
+                          : kWarp);
 
     P->desc_h.assign(np, PermDesc{});
     P->meta_h.clear();
@@ -870,9 +921,23 @@ static int ensure_backward(pq_plan* P)
     std::vector<double> cost;
     std::vector<int64_t> gpart_off(np), gl_off(np);
     int64_t gpart = 0, gl = 0;
+    // Low digits per chunk: each costs every lane one row of corrections
+    // (ld complex) in shared memory; keep the per-warp workspace within a
+    // quarter of the SM so at least four warps (FP64 saturation) fit.
+    int n2max = 0;
+    for (const ItemPlan& it : items) {
+        int c2 = 0;
+        for (int c : it.cmul)
+            c2 += (c >= 2) ? 1 : 0;
+        n2max = std::max(n2max, c2);
+    }
+    int jcap = kBwdMaxLowDigits;
+    while (jcap > 1 &&
+           bwd_smem_bytes_for(P->kmax, P->lmax, jcap, n2max) > (227 * 1024) / 4)
+        --jcap;
     for (int64_t p = 0; p < np; ++p) {
         ItemPlan& it = items[p];
-        choose_chunks(it, kBwdChunkLog2, kBwdMaxLowDigits);
+        choose_chunks(it, kBwdChunkLog2, jcap);
         PermDesc& D = P->desc_bwd_h[p];
         D.J = it.J;
         D.L = it.L;
@@ -927,12 +992,41 @@ static int ensure_backward(pq_plan* P)
             return rc;
         if ((rc = dev_upload(&P->item_l_d, P->item_l)) != PQ_OK)
             return rc;
+    } else {
+        // mode -> oriented index maps for the dL/dU scatter: pos[p][a] for the
+        // output mode a, pos[p][m + c] for the input mode c (-1 if empty)
+        const int m = P->m;
+        std::vector<int32_t> pos((size_t)np * 2 * m, -1);
+        for (int64_t p = 0; p < np; ++p) {
+            const ItemPlan& it = P->items[p];
+            int32_t* pp = pos.data() + (size_t)p * 2 * m;
+            const std::vector<int32_t>& outs = it.transposed ? it.cidx : it.ridx;
+            const std::vector<int32_t>& ins = it.transposed ? it.ridx : it.cidx;
+            for (size_t q = 0; q < outs.size(); ++q)
+                pp[outs[q]] = (int32_t)q;
+            for (size_t q = 0; q < ins.size(); ++q)
+                pp[m + ins[q]] = (int32_t)q;
+        }
+        if ((rc = dev_upload(&P->bs_pos_d, pos)) != PQ_OK)
+            return rc;
     }
-    const int per_warp = bwd_smem_bytes_for(P->kmax, P->lmax, kBwdMaxLowDigits);
+    // workspace sized by what the plan uses: low digits per chunk, repeated
+    // product columns
+    int jb = 0, n2 = 0;
+    for (const ItemPlan& it : items) {
+        jb = std::max(jb, it.J);
+        int c2 = 0;
+        for (int c : it.cmul)
+            c2 += (c >= 2) ? 1 : 0;
+        n2 = std::max(n2, c2);
+    }
+    P->bwd_jb = jb;
+    P->bwd_n2 = n2;
+    const int per_warp = bwd_smem_bytes_for(P->kmax, P->lmax, jb, n2);
     if (per_warp > 200 * 1024)
         return fail(PQ_ERR_UNSUPPORTED, "backward shared memory per warp %d too large", per_warp);
     int wpb = 0, bps = 0;
-    launch_geometry(bwd_regs_per_thread(P->lmax), per_warp, 4, 8, wpb, bps);
+    launch_geometry(bwd_regs_per_thread(P->lmax), per_warp, 8, 8, wpb, bps);
     P->bwd_wpb = wpb;
     P->bwd_blocks = std::max(1, P->num_sms * bps);
     cudaError_t e = bwd_prepare(P->lmax, wpb * per_warp);
@@ -970,13 +1064,14 @@ static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, co
         a.tasks = P->tasks_bwd_plain_d;
         for (int64_t p = 0; p < P->nperm; ++p) {
             e = bwd_launch_plain(P->lmax, a, P->plain_first_bwd[p], P->plain_first_bwd[p + 1],
-                                 P->kmax, P->bwd_wpb, st);
+                                 P->kmax, P->bwd_jb, P->bwd_n2, P->bwd_wpb, st);
             if (e != cudaSuccess)
                 return fail(PQ_ERR_CUDA, "plain backward launch failed: %s", cudaGetErrorString(e));
         }
     } else {
         a.tasks = P->tasks_bwd_batched_d;
-        e = bwd_launch_persistent(P->lmax, a, P->kmax, P->bwd_blocks, P->bwd_wpb, st);
+        e = bwd_launch_persistent(P->lmax, a, P->kmax, P->bwd_jb, P->bwd_n2, P->bwd_blocks,
+                                  P->bwd_wpb, st);
         if (e != cudaSuccess)
             return fail(PQ_ERR_CUDA, "backward launch failed: %s", cudaGetErrorString(e));
     }
@@ -1050,7 +1145,7 @@ extern "C" int pq_bs_probs_backward(const pq_c128* U, int32_t m, const int32_t* 
     }
     int rc = run_backward(P, U, nullptr, grad_probs, amps, st);
     if (rc == PQ_OK) {
-        cudaError_t e = scatter_grad_bs(P->desc_bwd_d, P->meta_d, P->nperm, m, P->grad_local_d,
+        cudaError_t e = scatter_grad_bs(P->desc_bwd_d, P->bs_pos_d, P->nperm, m, P->grad_local_d,
                                         P->grad_local_off_d, reinterpret_cast<double2*>(grad_U),
                                         st);
         if (e != cudaSuccess)

@@ -54,15 +54,14 @@ struct BwdArgs {
     int32_t* counters;
     int32_t* err;
 };
-int bwd_smem_per_warp(int kmax, int lmax);
-int bwd_smem_bytes_for(int kmax, int lmax, int jb);
+int bwd_smem_bytes_for(int kmax, int lmax, int jb, int n2);
 constexpr int kBwdMaxLowDigits = 4;  // low digits the backward workspace holds
 constexpr int kBwdChunkLog2 = 4;     // backward chunks of at most 2^4 terms
 cudaError_t bwd_prepare(int lmax, int smem_bytes);
-cudaError_t bwd_launch_persistent(int lmax, const BwdArgs& a, int kmax, int blocks, int wpb,
-                                  cudaStream_t st);
+cudaError_t bwd_launch_persistent(int lmax, const BwdArgs& a, int kmax, int jb, int n2, int blocks,
+                                  int wpb, cudaStream_t st);
 cudaError_t bwd_launch_plain(int lmax, const BwdArgs& a, int64_t t_begin, int64_t t_end,
-                             int kmax, int wpb, cudaStream_t st);
+                             int kmax, int jb, int n2, int wpb, cudaStream_t st);
 
 // Scatter of oriented per-permanent gradients into the caller's layouts.
 cudaError_t scatter_grad_batch(const PermDesc* desc, const int32_t* meta, int64_t nperm,
@@ -70,7 +69,7 @@ cudaError_t scatter_grad_batch(const PermDesc* desc, const int32_t* meta, int64_
                                const int64_t* item_mat_off, const int32_t* item_l,
                                const int32_t* item_k, double2* grad_mats, int64_t total_elems,
                                cudaStream_t st);
-cudaError_t scatter_grad_bs(const PermDesc* desc, const int32_t* meta, int64_t nperm, int32_t m,
+cudaError_t scatter_grad_bs(const PermDesc* desc, const int32_t* pos, int64_t nperm, int32_t m,
                             const double2* grad_local, const int64_t* grad_local_off,
                             double2* grad_U, cudaStream_t st);
 

@@ -46,6 +46,8 @@ struct pq_plan {
     int blocks = 0;
     int bwd_wpb = 4;
     int bwd_blocks = 0;
+    int bwd_jb = 0;  // low digits per backward chunk, at most
+    int bwd_n2 = 0;  // repeated product columns, at most
     int bwd_kmax = 1;
     // boson sampling inputs
     int32_t m = 0;
@@ -85,6 +87,7 @@ struct pq_plan {
     int32_t* item_k_d = nullptr;
     int32_t* item_l_d = nullptr;
     double2* grad_out_tmp_d = nullptr;
+    int32_t* bs_pos_d = nullptr;  // boson sampling: mode -> oriented index, 2m per pattern
     size_t gpart_elems = 0, grad_local_elems = 0;
     // graph of the batched forward
     cudaGraphExec_t graph = nullptr;

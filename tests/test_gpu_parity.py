@@ -89,8 +89,8 @@ def test_random_batch_with_multiplicities(dev):
     got_b, _ = gpu_perms(pb, dev, "batched")
     got_p, _ = gpu_perms(pb, dev, "plain")
     assert rel_err(got_b, ref).max() <= TOL
-    # same plan layout -> same partial sums in the same order -> same bits
-    assert np.array_equal(got_b, got_p)
+    # the plain method cuts every permanent finer (one launch must fill the GPU)
+    assert rel_err(got_p, ref).max() <= TOL
 
 
 @pytest.mark.parametrize("chunk_log2", [1, 3, 6, 12])
@@ -358,7 +358,9 @@ def test_bs_backward_plain_matches_batched(dev):
         plan = api.Plan.for_bs(16, s, t, method=method)
         p, a = api.bs_probs(U, sd, td, plan)
         outs.append(api.bs_probs_backward(U, sd, td, g, a, plan).cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+    # the two methods chunk the forward differently, so the amplitudes fed to
+    # the backward may differ in the last bits
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-12 * np.abs(outs[0]).max()
 
 
 def test_fp64_probe_runs(dev):
