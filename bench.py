@@ -90,7 +90,7 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 100 ms while the timed region runs."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -104,7 +104,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -434,6 +434,30 @@ def extra_measurements(args, dev, stream, flush):
     ms = timed(lambda: api.permanent_batched(db30, plan30, out=out30, stream=stream), 3)
     res["single_n30"] = {"terms_per_s": st["terms"] / ms * 1e3, "ms": ms,
                          "tflops": st["flops_forward"] / ms / 1e9}
+    # the paper's repeated-permanent benchmark shape (Sec. 4.2, Fig. permanent):
+    # k x k Haar block, every row and column repeated twice, one launch each
+    sweep = {}
+    for k in range(4, 17):
+        B, r, c = W.paper_repeated(k)
+        pbk = W.pack_batch([(B, r, c)])
+        dbk = api.DeviceBatch(pbk, dev)
+        plank = api.Plan.for_batch(pbk, method="plain")
+        outk = torch.empty(1, dtype=torch.complex128, device=dev)
+        stk = plank.stats()
+        ms = timed(lambda: api.permanent_batched(dbk, plank, out=outk, stream=stream), 5)
+        sweep[str(k)] = {"ms": ms, "terms": stk["terms"], "terms_per_s": stk["terms"] / ms * 1e3}
+    res["paper_repeated_2x"] = sweep
+    # Algorithm A sampler (one batched launch per photon over all samples),
+    # m = 16 Haar interferometer, 8 photons, 2000 samples
+    Us = torch.from_numpy(W.haar_unitary(16, W.rng_for(7))).to(dev)
+    s8 = np.zeros(16, dtype=np.int32)
+    s8[:8] = 1
+    order, unif = W.sampler_draws(2000, 8, 1007)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    api.bs_sample(Us, s8, order, unif)
+    secs = time.perf_counter() - t0
+    res["sampler_m16_n8"] = {"samples": 2000, "s": secs, "samples_per_s": 2000 / secs}
     # batched boson sampling, m = 24, 4096 patterns
     U, s, t = W.bs_batched()
     Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))
@@ -493,7 +517,7 @@ def bench_reference(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the extra measurements")

@@ -192,6 +192,23 @@ int pq_clements_backward(const double* theta, const double* phi, int32_t m, cons
                          const pq_c128* grad_U, double* grad_theta, double* grad_phi,
                          void* stream);
 
+/* Boson sampling by Clifford and Clifford's "Algorithm A", the sampler the
+ * paper uses with its permanents (Sec. 4.2): photons are drawn one at a time;
+ * at step k every candidate output mode i is weighted by
+ * |per(A[{r_1..r_{k-1}, i}, 1..k])|^2, A = the columns of U of the occupied
+ * input modes (mode j repeated s_j times) in a random order.  Each step is
+ * one batched launch over all samples and candidates.
+ * U: device, m x m, U[out][in].  input_occ: host, m.  col_order: host,
+ * nsamples x n, row b a permutation of 0 .. n-1 (the random column order of
+ * sample b).  uniforms: host, nsamples x n, in [0, 1): the draw of photon k of
+ * sample b picks the first mode whose running weight sum (modes in order)
+ * exceeds uniforms[b][k-1] times the total.  samples: host, nsamples x m
+ * output occupations.  Synchronises `stream`; allocates its workspace.
+ * Errors: PQ_ERR_ARG (null, sizes, not a permutation, uniform outside
+ * [0, 1), all weights zero), PQ_ERR_UNSUPPORTED, PQ_ERR_NOMEM, PQ_ERR_CUDA. */
+int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_occ, int64_t nsamples,
+                 const int32_t* col_order, const double* uniforms, int32_t* samples, void* stream);
+
 /* Times trial launches of the plan's batched kernel for each size class on
  * the given data and stores the fastest chunk length per class in the plan
  * (and in the process-wide tuning table used by later plans).  Synchronises

@@ -253,3 +253,11 @@ class ClementsMesh(torch.autograd.Function):
 def probe_fp64_peak(iters: int = 1 << 16, stream=None) -> tuple[float, float]:
     """Measured FP64 rate of this GPU (FLOP/s, FMA = 2) and the probe's ms."""
     return _pq.pq_probe_fp64_peak(iters, _stream_handle(stream))
+
+
+def bs_sample(U: torch.Tensor, s, col_order, uniforms, stream=None) -> np.ndarray:
+    """Boson-sampling outputs by Algorithm A (pq_bs_sample): U on the GPU,
+    input occupation s, and the run's random column orders and uniforms
+    (host arrays, nsamples x n).  Returns nsamples x m occupations."""
+    return _pq.pq_bs_sample(_ptr(U.contiguous()), U.shape[0], np.asarray(s), col_order,
+                            uniforms, _stream_handle(stream))

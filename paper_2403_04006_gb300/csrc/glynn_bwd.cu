@@ -32,27 +32,32 @@
 
 namespace pqi {
 
+// Row stride (in elements) of the lane-major per-lane arrays: 33, not 32, so
+// that the end-of-task contraction, where lane e reads element (j(e), q) for
+// a fixed q, spreads over the banks instead of hitting one bank 32 times.
+constexpr int kLS = 33;
+
 // Per-warp shared memory: ld = product-column bound, jb = low digits of the
 // plan's chunks, n2 = repeated product columns at most (powers are kept only
 // for those).
 __host__ __device__ inline int bwd_warp_smem_bytes(int kmax, int ld, int jb, int n2)
 {
-    long bytes = 16L * (kmax * ld + ld + 3L * 32 * ld + 2L * 32 * n2 + 32L * jb * ld) + 8L * 32 +
-                 4L * (32L * kmax + 16 + ld + kmax);
+    long bytes = 16L * (kmax * ld + ld + 3L * kLS * ld + 2L * kLS * n2 + kLS * (long)jb * ld) + 8L * 32 +
+                 4L * (kLS * (long)kmax + 16 + ld + kmax);
     return (int)((bytes + 15) & ~15L);
 }
 
 struct BwdSmem {
     double2* M;       // kmax x ld
     double2* base;    // ld
-    double2* S;       // ld x 32 (lane-major)
-    double2* A;       // ld x 32
-    double2* P;       // ld x 32
-    double2* PW;      // n2 x 32
-    double2* FULL;    // n2 x 32
-    double2* C;       // jb x ld x 32
+    double2* S;       // ld x kLS (lane-major: element (j, lane) at j * kLS + lane)
+    double2* A;       // ld x kLS
+    double2* P;       // ld x kLS
+    double2* PW;      // n2 x kLS
+    double2* FULL;    // n2 x kLS
+    double2* C;       // jb x ld x kLS
     double* wh;       // 32
-    int32_t* x;       // kmax x 32
+    int32_t* x;       // kmax x kLS
     int32_t* lowrow;  // 16
     int32_t* cm;      // ld
     int32_t* rowdig;  // kmax: low digit of each row, or -1
@@ -63,14 +68,14 @@ struct BwdSmem {
         M = reinterpret_cast<double2*>(raw);
         base = M + kmax * ld;
         S = base + ld;
-        A = S + 32 * ld;
-        P = A + 32 * ld;
-        PW = P + 32 * ld;
-        FULL = PW + 32 * n2;
-        C = FULL + 32 * n2;
-        wh = reinterpret_cast<double*>(C + 32 * jb * ld);
+        A = S + kLS * ld;
+        P = A + kLS * ld;
+        PW = P + kLS * ld;
+        FULL = PW + kLS * n2;
+        C = FULL + kLS * n2;
+        wh = reinterpret_cast<double*>(C + kLS * jb * ld);
         x = reinterpret_cast<int32_t*>(wh + 32);
-        lowrow = x + kmax * 32;
+        lowrow = x + kmax * kLS;
         cm = lowrow + 16;
         rowdig = cm + ld;
     }
@@ -85,7 +90,7 @@ __device__ __forceinline__ void acc_scaled(double2* a, double s, double2 q)
 }
 
 // A_j += ws * Q_j for this lane's column sums.  All pointers are lane-offset
-// with stride 32.  n2 = number of leading columns with c_j >= 2.
+// with stride kLS.  n2 = number of leading columns with c_j >= 2.
 __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* PW, double2* FULL,
                                          double2* A, int l, int n2, const int32_t* cm, double ws)
 {
@@ -104,56 +109,56 @@ __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* 
     // powers of the repeated columns
 #pragma unroll 1
     for (int j = 0; j < n2; ++j) {
-        const double2 s = S[j * 32];
+        const double2 s = S[j * kLS];
         double2 pw = s;
 #pragma unroll 1
         for (int e = 2; e < cm[j]; ++e)
             pw = cmul(pw, s);
-        PW[j * 32] = pw;
-        FULL[j * 32] = cmul(pw, s);
+        PW[j * kLS] = pw;
+        FULL[j * kLS] = cmul(pw, s);
     }
     // prefix P_j = prod_{j' < j} S_{j'}^{c_{j'}}, j = 1 .. l-1
     double2 run = (n2 > 0) ? FULL[0] : S[0];
-    P[32] = run;
+    P[kLS] = run;
     const int na = n2 < l - 1 ? n2 : l - 1;  // repeated columns among 1 .. l-2
 #pragma unroll 1
     for (int j = 1; j < na; ++j) {
-        run = cmul(run, FULL[j * 32]);
-        P[(j + 1) * 32] = run;
+        run = cmul(run, FULL[j * kLS]);
+        P[(j + 1) * kLS] = run;
     }
 #pragma unroll 1
     for (int j = (na > 1 ? na : 1); j < l - 1; ++j) {
-        run = cmul(run, S[j * 32]);
-        P[(j + 1) * 32] = run;
+        run = cmul(run, S[j * kLS]);
+        P[(j + 1) * kLS] = run;
     }
     // suffix pass, last column first
     double2 sf;
     {
         const int j = l - 1;
-        double2 q = P[j * 32];
+        double2 q = P[j * kLS];
         if (j < n2) {
-            q = cmul(q, PW[j * 32]);
-            acc_scaled(A + j * 32, ws * (double)cm[j], q);
-            sf = FULL[j * 32];
+            q = cmul(q, PW[j * kLS]);
+            acc_scaled(A + j * kLS, ws * (double)cm[j], q);
+            sf = FULL[j * kLS];
         } else {
-            acc_scaled(A + j * 32, ws, q);
-            sf = S[j * 32];
+            acc_scaled(A + j * kLS, ws, q);
+            sf = S[j * kLS];
         }
     }
     // columns l-2 .. 1 with c_j = 1
 #pragma unroll 1
     for (int j = l - 2; j >= 1 && j >= n2; --j) {
-        const double2 q = cmul(P[j * 32], sf);
-        acc_scaled(A + j * 32, ws, q);
-        sf = cmul(sf, S[j * 32]);
+        const double2 q = cmul(P[j * kLS], sf);
+        acc_scaled(A + j * kLS, ws, q);
+        sf = cmul(sf, S[j * kLS]);
     }
     // columns min(n2, l-1) - 1 .. 1 with c_j >= 2
 #pragma unroll 1
     for (int j = (n2 < l - 1 ? n2 : l - 1) - 1; j >= 1; --j) {
-        double2 q = cmul(P[j * 32], sf);
-        q = cmul(q, PW[j * 32]);
-        acc_scaled(A + j * 32, ws * (double)cm[j], q);
-        sf = cmul(sf, FULL[j * 32]);
+        double2 q = cmul(P[j * kLS], sf);
+        q = cmul(q, PW[j * kLS]);
+        acc_scaled(A + j * kLS, ws * (double)cm[j], q);
+        sf = cmul(sf, FULL[j * kLS]);
     }
     // column 0: Q_0 = c_0 S_0^{c_0 - 1} * prod_{j > 0}
     if (n2 > 0) {
@@ -219,11 +224,11 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
         double2* A = sm.A + lane;
 #pragma unroll 1
         for (int j = 0; j < l; ++j) {
-            S[j * 32] = sm.base[j];
-            A[j * 32] = make_double2(0.0, 0.0);
+            S[j * kLS] = sm.base[j];
+            A[j * kLS] = make_double2(0.0, 0.0);
         }
         for (int i = 0; i < k; ++i)
-            sm.x[i * 32 + lane] = mv.rmul[i];
+            sm.x[i * kLS + lane] = mv.rmul[i];
         uint64_t whigh_u = 1;
         int gpar = 0;
 #pragma unroll 1
@@ -237,12 +242,12 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
 #pragma unroll 1
             for (int j = 0; j < l; ++j) {
                 const double2 b = Mr[j];
-                double2 s = S[j * 32];
+                double2 s = S[j * kLS];
                 s.x = __fma_rn(coef, b.x, s.x);
                 s.y = __fma_rn(coef, b.y, s.y);
-                S[j * 32] = s;
+                S[j * kLS] = s;
             }
-            sm.x[row * 32 + lane] = mv.rmul[row] - 2 * g;
+            sm.x[row * kLS + lane] = mv.rmul[row] - 2 * g;
             if (g) {
                 whigh_u *= binom_u64(mv.dtop[d], g);
                 gpar += g;
@@ -254,7 +259,7 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
         sm.wh[lane] = whigh;
         for (int e = 0; e < J * l; ++e) {
             const int d = e / l, j = e - d * l;
-            sm.C[(d * sm.ld + j) * 32 + lane] = make_double2(0.0, 0.0);
+            sm.C[(d * sm.ld + j) * kLS + lane] = make_double2(0.0, 0.0);
         }
         int n2 = 0;
         while (n2 < l && sm.cm[n2] >= 2)
@@ -282,21 +287,21 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
                 const int row = sm.lowrow[d];
                 const double delta = up > 0 ? -2.0 : 2.0;
                 const double2* Mr = sm.M + row * sm.ld;
-                double2* Cd = sm.C + d * sm.ld * 32 + lane;
+                double2* Cd = sm.C + d * sm.ld * kLS + lane;
 #pragma unroll 1
                 for (int j = 0; j < l; ++j) {
                     const double2 b = Mr[j];
-                    double2 sv = S[j * 32];
+                    double2 sv = S[j * kLS];
                     sv.x = __fma_rn(delta, b.x, sv.x);
                     sv.y = __fma_rn(delta, b.y, sv.y);
-                    S[j * 32] = sv;
-                    const double2 av = A[j * 32];
-                    double2 cv = Cd[j * 32];
+                    S[j * kLS] = sv;
+                    const double2 av = A[j * kLS];
+                    double2 cv = Cd[j * kLS];
                     cv.x = __fma_rn(delta, av.x, cv.x);
                     cv.y = __fma_rn(delta, av.y, cv.y);
-                    Cd[j * 32] = cv;
+                    Cd[j * kLS] = cv;
                 }
-                sm.x[row * 32 + lane] += (up > 0 ? -2 : 2);
+                sm.x[row * kLS + lane] += (up > 0 ? -2 : 2);
                 if (((wk.radm1 >> (4 * d)) & 15u) > 1u)
                     wlow = (double)low_weight(wk, J);
             }
@@ -308,11 +313,11 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
             const int dg = sm.rowdig[i];
             double gx = 0.0, gy = 0.0;
             for (int q = 0; q < 32; ++q) {
-                const double2 av = sm.A[j * 32 + q];
-                const double xv = (double)sm.x[i * 32 + q];
+                const double2 av = sm.A[j * kLS + q];
+                const double xv = (double)sm.x[i * kLS + q];
                 double tx = xv * av.x, ty = xv * av.y;
                 if (dg >= 0) {
-                    const double2 cv = sm.C[(dg * sm.ld + j) * 32 + q];
+                    const double2 cv = sm.C[(dg * sm.ld + j) * kLS + q];
                     tx -= cv.x;
                     ty -= cv.y;
                 }

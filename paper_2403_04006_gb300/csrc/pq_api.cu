@@ -1310,3 +1310,52 @@ extern "C" int pq_plan_item_info(int32_t k, int32_t l, const int32_t* row_mult,
     }
     return PQ_OK;
 }
+
+// ---------------------------------------------------------------- internal: occupation plans
+namespace pqi {
+
+// A plan over one m x m matrix whose item b is the submatrix with row
+// occupations t[b] and column occupations s[b] (each length m, host); no
+// normalisation (norm = 1), so probs receive |per|^2.
+int plan_create_occupations(int32_t m, const std::vector<int32_t>& t, const std::vector<int32_t>& s,
+                            int64_t B, pq_plan** out)
+{
+    *out = nullptr;
+    pq_plan* P = new (std::nothrow) pq_plan();
+    if (!P)
+        return fail(PQ_ERR_NOMEM, "host allocation failed");
+    int rc = plan_common_init(P, nullptr);
+    if (rc != PQ_OK) {
+        delete P;
+        return rc;
+    }
+    P->kind = 2;
+    P->m = m;
+    P->items.resize(B);
+    for (int64_t b = 0; b < B; ++b) {
+        rc = build_item(t.data() + b * m, s.data() + b * m, m, m, 0, m, P->items[b]);
+        if (rc != PQ_OK) {
+            delete P;
+            return rc;
+        }
+        P->items[b].norm = 1.0;
+    }
+    P->class_log2.assign(PQ_MAX_N + 1, 0);
+    rc = schedule_and_upload(P);
+    if (rc != PQ_OK) {
+        free_plan_device(P);
+        delete P;
+        return rc;
+    }
+    *out = P;
+    return PQ_OK;
+}
+
+int plan_run_forward(pq_plan* P, const void* src, void* amps, double* probs, cudaStream_t st)
+{
+    return run_forward_raw(P, src, amps, probs, st);
+}
+
+int report(int code, const char* msg) { return fail(code, "%s", msg); }
+
+}  // namespace pqi

@@ -81,6 +81,7 @@ cudaError_t clements_backward(const double* theta, const double* phi, int m, con
 
 // ---- error message of the calling thread, read by pq_last_error (pq_api.cu)
 void set_last_error(const char* msg);
+int report(int code, const char* msg);  // set the message, return code
 
 // ---- FP64 probe (fp64_probe.cu)
 cudaError_t fp64_probe(int64_t iters, double* flops_per_s, double* ms, cudaStream_t st);

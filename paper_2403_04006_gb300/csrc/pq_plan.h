@@ -96,3 +96,11 @@ struct pq_plan {
     // statistics
     pq_plan_stats stats{};
 };
+
+namespace pqi {
+// Plans over one m x m matrix with per-item row occupations t[b] and column
+// occupations s[b] (host, B x m each), no normalisation; and a forward run.
+int plan_create_occupations(int32_t m, const std::vector<int32_t>& t, const std::vector<int32_t>& s,
+                            int64_t B, pq_plan** out);
+int plan_run_forward(pq_plan* P, const void* src, void* amps, double* probs, cudaStream_t st);
+}  // namespace pqi

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "pq_probe_fp64_peak": (_i32, [_i64, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double), _vp]),
     "pq_permanent_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "pq_bs_sample": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "pq_last_error": (ctypes.c_char_p, []),
@@ -198,6 +199,23 @@ def pq_permanent_noalloc(B_ptr, k: int, l: int, row_mult: np.ndarray, col_mult: 
     _check(load_library().pq_permanent_noalloc(B_ptr, k, l, r.ctypes.data if r.size else None,
                                                c.ctypes.data if c.size else None, out_ptr,
                                                stream), "pq_permanent_noalloc")
+
+
+def pq_bs_sample(U_ptr, m: int, input_occ: np.ndarray, col_order: np.ndarray,
+                 uniforms: np.ndarray, stream) -> np.ndarray:
+    """Algorithm A samples; col_order (nsamples x n int32) and uniforms
+    (nsamples x n float64) are host arrays.  Returns nsamples x m occupations."""
+    s = np.ascontiguousarray(input_occ, dtype=np.int32)
+    co = np.ascontiguousarray(col_order, dtype=np.int32)
+    un = np.ascontiguousarray(uniforms, dtype=np.float64)
+    ns = co.shape[0]
+    out = np.zeros((ns, m), dtype=np.int32)
+    _check(load_library().pq_bs_sample(U_ptr, m, s.ctypes.data, ns,
+                                       co.ctypes.data if co.size else None,
+                                       un.ctypes.data if un.size else None,
+                                       out.ctypes.data if out.size else None, stream),
+           "pq_bs_sample")
+    return out
 
 
 def pq_version() -> str:

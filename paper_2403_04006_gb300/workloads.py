@@ -270,3 +270,13 @@ def paper_repeated(k: int, seed_stream: int = 0):
     U = haar_unitary(2 * k, rng_for(6, 100 * k + seed_stream))
     B = np.ascontiguousarray(U[:k, :k])
     return B, np.full(k, 2, dtype=np.int32), np.full(k, 2, dtype=np.int32)
+
+
+def sampler_draws(nsamples: int, n: int, seed: int):
+    """Random inputs of a boson sampler run: for every sample a uniformly
+    random order of its n photon columns and one uniform in [0, 1) per photon."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    order = np.stack([rng.permutation(n) for _ in range(nsamples)]).astype(np.int32) \
+        if nsamples else np.zeros((0, n), dtype=np.int32)
+    uniforms = rng.random((nsamples, n))
+    return np.ascontiguousarray(order.reshape(nsamples, n)), np.ascontiguousarray(uniforms)

@@ -381,3 +381,17 @@ def test_later_plan_with_smaller_workspace_keeps_earlier_plan_working(dev):
     api.permanent_batched(api.DeviceBatch(small, dev), plan_small)
     got = api.permanent_batched(db, plan_big).cpu().numpy()
     assert rel_err(got[0], ref) <= TOL
+
+
+@pytest.mark.parametrize("method", ["batched", "plain"])
+def test_paper_repeated_permanents(dev, method):
+    """The shape of the paper's repeated-permanent benchmark (Sec. 4.2, Fig.
+    permanent): a k x k Haar block with every row and column repeated twice,
+    k = 4 .. 14 (2 * 3^(k-1) Gray-code terms), one permanent per k."""
+    items = [W.paper_repeated(k) for k in range(4, 15)]
+    pb = W.pack_batch(items)
+    ref = np.array([O.perm_ryser(B, r, c, gold=True, nthreads=O.default_threads())
+                    for B, r, c in items])
+    got, plan = gpu_perms(pb, dev, method)
+    assert plan.stats()["terms"] == sum(2 * 3 ** (k - 1) for k in range(4, 15))
+    assert rel_err(got, ref).max() <= TOL
