@@ -192,6 +192,21 @@ int pq_clements_backward(const double* theta, const double* phi, int32_t m, cons
                          const pq_c128* grad_U, double* grad_theta, double* grad_phi,
                          void* stream);
 
+/* Boson-sampling probabilities with losses (Sec. 3.2.4, Fig. BS_LossModel):
+ * the interferometer A = V diag(sqrt(eta)) W (V, W unitary, eta_i in [0, 1]
+ * the transmission of mode i) loses photons to one inaccessible mode per
+ * mode through a beamsplitter, and p(t) is the probability that the m system
+ * detectors see t (|t| <= n; the rest were lost): the marginal of Eq.
+ * (BS_prob) on the 2m-mode unitary dilation over every occupation of the loss
+ * modes.  V, W: device, m x m (U[out][in] convention, A = V diag W); eta:
+ * device, m doubles; input_occ: host, m; output_occ: host, B x m; probs:
+ * device, B doubles.  2m <= PQ_MAX_DIM.  Allocates its workspace and
+ * synchronises `stream`.  Errors: PQ_ERR_ARG (null, negative, |t| > n),
+ * PQ_ERR_UNSUPPORTED (sizes), PQ_ERR_NOMEM, PQ_ERR_CUDA. */
+int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c128* W, int32_t m,
+                      const int32_t* input_occ, const int32_t* output_occ, int64_t B,
+                      double* probs, void* stream);
+
 /* Boson sampling by Clifford and Clifford's "Algorithm A", the sampler the
  * paper uses with its permanents (Sec. 4.2): photons are drawn one at a time;
  * at step k every candidate output mode i is weighted by

@@ -39,6 +39,7 @@ import numpy as np
 from .clements import (clements_layout, beamsplitter_block, clements_unitary,  # noqa: F401
                        clements_grad)
 from .sampler import algorithm_a  # noqa: F401
+from .lossy import lossy_probs  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pq_oracle.c")

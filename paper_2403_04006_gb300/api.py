@@ -255,6 +255,18 @@ def probe_fp64_peak(iters: int = 1 << 16, stream=None) -> tuple[float, float]:
     return _pq.pq_probe_fp64_peak(iters, _stream_handle(stream))
 
 
+def bs_probs_lossy(V: torch.Tensor, eta: torch.Tensor, W: torch.Tensor, s, t,
+                   stream=None) -> torch.Tensor:
+    """Detection probabilities of the lossy interferometer V diag(sqrt(eta)) W
+    for input occupation s and output patterns t (host arrays, |t| <= n)."""
+    t = np.atleast_2d(np.asarray(t, dtype=np.int32))
+    m = V.shape[0]
+    probs = torch.empty(t.shape[0], dtype=torch.float64, device=V.device)
+    _pq.pq_bs_probs_lossy(_ptr(V.contiguous()), _ptr(eta.contiguous()), _ptr(W.contiguous()), m,
+                          np.asarray(s), t, _ptr(probs), _stream_handle(stream))
+    return probs
+
+
 def bs_sample(U: torch.Tensor, s, col_order, uniforms, stream=None) -> np.ndarray:
     """Boson-sampling outputs by Algorithm A (pq_bs_sample): U on the GPU,
     input occupation s, and the run's random column orders and uniforms

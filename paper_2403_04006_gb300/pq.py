@@ -73,6 +73,7 @@ _SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_double), _vp]),
     "pq_permanent_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp]),
     "pq_bs_sample": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "pq_bs_probs_lossy": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp]),
     "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "pq_last_error": (ctypes.c_char_p, []),
@@ -216,6 +217,14 @@ def pq_bs_sample(U_ptr, m: int, input_occ: np.ndarray, col_order: np.ndarray,
                                        out.ctypes.data if out.size else None, stream),
            "pq_bs_sample")
     return out
+
+
+def pq_bs_probs_lossy(V_ptr, eta_ptr, W_ptr, m: int, input_occ: np.ndarray,
+                      output_occ: np.ndarray, probs_ptr, stream):
+    s = np.ascontiguousarray(input_occ, dtype=np.int32)
+    t = np.ascontiguousarray(output_occ, dtype=np.int32).reshape(-1, m)
+    _check(load_library().pq_bs_probs_lossy(V_ptr, eta_ptr, W_ptr, m, s.ctypes.data, t.ctypes.data,
+                                            t.shape[0], probs_ptr, stream), "pq_bs_probs_lossy")
 
 
 def pq_version() -> str:
