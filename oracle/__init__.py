@@ -83,8 +83,11 @@ def _load():
         lib.oracle_perm_batch.argtypes = [i64, dp, lp, ip, ip, ip, lp, ip, lp, ci, ci, dp]
         lib.oracle_bs_probs.argtypes = [dp, ci, ip, ip, i64, ci, ci, dp, dp]
         lib.oracle_bs_grad_U.argtypes = [dp, ci, ip, ip, i64, dp, ci, dp]
+        lib.oracle_haf_bruteforce.argtypes = [dp, ci, dp]
+        lib.oracle_haf_grouped.argtypes = [dp, ci, ip, dp]
         for f in ("oracle_perm_bruteforce", "oracle_perm_ryser", "oracle_perm_grad",
-                  "oracle_perm_batch", "oracle_bs_probs", "oracle_bs_grad_U"):
+                  "oracle_perm_batch", "oracle_bs_probs", "oracle_bs_grad_U",
+                  "oracle_haf_bruteforce", "oracle_haf_grouped"):
             getattr(lib, f).restype = ci
         _lib = lib
         return lib
@@ -206,6 +209,28 @@ def bs_probs(U, s, t, gold: bool = False, nthreads: int | None = None):
     _check(_load().oracle_bs_probs(_dptr(U), m, _iptr(s), _iptr(t), B, int(gold), nt,
                                    _dptr(probs), _dptr(amps)), "bs_probs")
     return probs, amps
+
+
+def haf_bruteforce(a) -> complex:
+    """haf(a) as the sum over perfect matchings of prod a_ij, Eq. (haf_def);
+    a symmetric, even size <= 16."""
+    a = _c128(a)
+    N = a.shape[0]
+    out = np.zeros(3)
+    _check(_load().oracle_haf_bruteforce(_dptr(a), N, _dptr(out)), "haf_bruteforce")
+    return complex(out[0], out[1])
+
+
+def haf_grouped(b, r=None, info: bool = False):
+    """Hafnian of the matrix repeating base index i r[i] times, by the grouped
+    sign-vector formula in double-double (every term from scratch)."""
+    b = _c128(b)
+    k = b.shape[0]
+    r = _i32(np.ones(k) if r is None else r)
+    out = np.zeros(3)
+    _check(_load().oracle_haf_grouped(_dptr(b), k, _iptr(r), _dptr(out)), "haf_grouped")
+    h = complex(out[0], out[1])
+    return (h, float(out[2])) if info else h
 
 
 def bs_grad_U(U, s, t, grad_probs, gold: bool = False) -> np.ndarray:

@@ -804,3 +804,148 @@ int oracle_bs_grad_U(const double *U, int m, const int *s, const int *t, int64_t
     free(G);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* hafnian, Eq. (haf_def)                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Sum over perfect matchings: the lowest unmatched index is paired with every
+ * later unmatched one in turn (each matching is visited once). */
+static void haf_rec(const double *a, int N, int *used, cd_t prod, dd_t *acc_re, dd_t *acc_im,
+                    double *sumabs)
+{
+    int p = 0, q;
+    while (p < N && used[p])
+        p++;
+    if (p == N) {
+        *acc_re = dd_add(*acc_re, dd_from(prod.re));
+        *acc_im = dd_add(*acc_im, dd_from(prod.im));
+        *sumabs += hypot(prod.re, prod.im);
+        return;
+    }
+    used[p] = 1;
+    for (q = p + 1; q < N; q++) {
+        cd_t x, np;
+        if (used[q])
+            continue;
+        used[q] = 1;
+        x.re = a[2 * (p * N + q)];
+        x.im = a[2 * (p * N + q) + 1];
+        np = cd_mul(prod, x);
+        haf_rec(a, N, used, np, acc_re, acc_im, sumabs);
+        used[q] = 0;
+    }
+    used[p] = 0;
+}
+
+/* a: N x N complex symmetric (only the upper triangle is read), N even,
+ * N <= 16.  out[0..1] = haf(a), out[2] = sum |term|.  haf of size 0 is 1. */
+int oracle_haf_bruteforce(const double *a, int N, double *out)
+{
+    int used[16] = {0};
+    dd_t re = dd_from(0.0), im = dd_from(0.0);
+    double sumabs = 0.0;
+    cd_t one = {1.0, 0.0};
+    if (N < 0 || N > 16 || (N & 1) || out == NULL || (N > 0 && a == NULL))
+        return ORC_ERR_ARG;
+    haf_rec(a, N, used, one, &re, &im, &sumabs);
+    out[0] = re.hi + re.lo;
+    out[1] = im.hi + im.lo;
+    out[2] = sumabs;
+    return ORC_OK;
+}
+
+/* Hafnian of the matrix that repeats base index i r_i times (rows and
+ * columns), N = sum r even, by the grouped sign-vector formula
+ *   haf = 1 / (n! 2^{N-1}) sum_g (-1)^{sum g} C(r_f - 1, g_f) prod_{i != f} C(r_i, g_i) q(g)^n,
+ *   q(g) = 1/2 (x^T B x - sum_i r_i B_ii),  x_i = r_i - 2 g_i,  n = N / 2,
+ * with g_f in [0, r_f - 1] for the first index f with r_f > 0 (one copy's sign
+ * fixed), every q evaluated from scratch in double-double, every term added
+ * in double-double.  It follows from Eq. (haf_def): the mean over all sign
+ * vectors d of (prod d) (sum_{p<q} A_pq d_p d_q)^n is n! haf(A), and the
+ * vectors that put g_i minus signs on the copies of index i all give the same
+ * x.  b: k x k complex symmetric.  out[0..1] = haf, out[2] = sum |term| / (n! 2^{N-1}). */
+int oracle_haf_grouped(const double *b, int k, const int *r, double *out)
+{
+    int i, j, N = 0, f = -1, kd[64];
+    int64_t T = 1, rank;
+    dd_t acc_re = dd_from(0.0), acc_im = dd_from(0.0);
+    double sumabs = 0.0, scale;
+    cd_t dsum;
+    if (k < 0 || k > 64 || out == NULL || (k > 0 && (b == NULL || r == NULL)))
+        return ORC_ERR_ARG;
+    for (i = 0; i < k; i++) {
+        if (r[i] < 0)
+            return ORC_ERR_ARG;
+        N += r[i];
+        if (f < 0 && r[i] > 0)
+            f = i;
+    }
+    if (N & 1) {
+        out[0] = out[1] = out[2] = 0.0;
+        return ORC_OK;
+    }
+    if (N == 0) {
+        out[0] = 1.0;
+        out[1] = 0.0;
+        out[2] = 1.0;
+        return ORC_OK;
+    }
+    if (N > 62)
+        return ORC_ERR_TOO_LARGE;
+    for (i = 0; i < k; i++) {
+        int64_t rad = (i == f) ? r[i] : r[i] + 1;
+        if (T > ((int64_t)1 << 62) / rad)
+            return ORC_ERR_TOO_LARGE;
+        T *= rad;
+    }
+    /* sum_i r_i B_ii */
+    dsum.re = 0.0;
+    dsum.im = 0.0;
+    for (i = 0; i < k; i++) {
+        dsum.re += r[i] * b[2 * (i * k + i)];
+        dsum.im += r[i] * b[2 * (i * k + i) + 1];
+    }
+    for (rank = 0; rank < T; rank++) {
+        int64_t rem = rank;
+        int gsum = 0;
+        double w = 1.0;
+        cdd_t xbx, q, p;
+        for (i = 0; i < k; i++) {
+            int rad = (i == f) ? r[i] : r[i] + 1;
+            kd[i] = (int)(rem % rad);
+            rem /= rad;
+            gsum += kd[i];
+            w *= (i == f) ? binom(r[i] - 1, kd[i]) : binom(r[i], kd[i]);
+        }
+        if (gsum & 1)
+            w = -w;
+        /* x^T B x in double-double */
+        xbx.re = dd_from(0.0);
+        xbx.im = dd_from(0.0);
+        for (i = 0; i < k; i++) {
+            double xi = (double)(r[i] - 2 * kd[i]);
+            for (j = 0; j < k; j++) {
+                dd_t c = dd_from(xi * (double)(r[j] - 2 * kd[j])); /* exact small integer */
+                xbx.re = dd_add(xbx.re, dd_mul(c, dd_from(b[2 * (i * k + j)])));
+                xbx.im = dd_add(xbx.im, dd_mul(c, dd_from(b[2 * (i * k + j) + 1])));
+            }
+        }
+        q.re = dd_mul(dd_add(xbx.re, dd_from(-dsum.re)), dd_from(0.5));
+        q.im = dd_mul(dd_add(xbx.im, dd_from(-dsum.im)), dd_from(0.5));
+        /* q^n by repeated multiplication */
+        p = q;
+        for (j = 1; j < N / 2; j++)
+            p = cdd_mul(p, q);
+        p.re = dd_mul(p.re, dd_from(w));
+        p.im = dd_mul(p.im, dd_from(w));
+        acc_re = dd_add(acc_re, p.re);
+        acc_im = dd_add(acc_im, p.im);
+        sumabs += hypot(p.re.hi, p.im.hi);
+    }
+    scale = ldexp(1.0, -(N - 1)) / factorial(N / 2);
+    out[0] = (acc_re.hi + acc_re.lo) * scale;
+    out[1] = (acc_im.hi + acc_im.lo) * scale;
+    out[2] = sumabs * scale;
+    return ORC_OK;
+}
