@@ -21,6 +21,10 @@ Functions and the passage each follows:
 * ``perm_batch``           -- the same, over a ragged batch.
 * ``perm_grad``            -- Laplace-minor derivative of Eq. (per_def).
 * ``bs_probs``             -- Eq. (BS_prob).
+* ``haf_*``                -- Eq. (haf_def), by matchings and by the grouped
+                              sign-vector formula for repeated indices (Sec. 4.1).
+* ``lhaf_*``               -- Eq. (loop_hafnian) with the filldiag of the
+                              displaced detection probability, the same two ways.
 * ``bs_grad_U``            -- chain rule through Eq. (BS_prob) and ``perm_grad``.
 * ``clements_*``           -- beamsplitter matrix of Appendix A "Beamsplitter gate",
                               arranged as a Clements mesh (layout is a reading, the
@@ -85,9 +89,12 @@ def _load():
         lib.oracle_bs_grad_U.argtypes = [dp, ci, ip, ip, i64, dp, ci, dp]
         lib.oracle_haf_bruteforce.argtypes = [dp, ci, dp]
         lib.oracle_haf_grouped.argtypes = [dp, ci, ip, dp]
+        lib.oracle_lhaf_bruteforce.argtypes = [dp, ci, dp]
+        lib.oracle_lhaf_grouped.argtypes = [dp, dp, ci, ip, dp]
         for f in ("oracle_perm_bruteforce", "oracle_perm_ryser", "oracle_perm_grad",
                   "oracle_perm_batch", "oracle_bs_probs", "oracle_bs_grad_U",
-                  "oracle_haf_bruteforce", "oracle_haf_grouped"):
+                  "oracle_haf_bruteforce", "oracle_haf_grouped", "oracle_lhaf_bruteforce",
+                  "oracle_lhaf_grouped"):
             getattr(lib, f).restype = ci
         _lib = lib
         return lib
@@ -229,6 +236,30 @@ def haf_grouped(b, r=None, info: bool = False):
     r = _i32(np.ones(k) if r is None else r)
     out = np.zeros(3)
     _check(_load().oracle_haf_grouped(_dptr(b), k, _iptr(r), _dptr(out)), "haf_grouped")
+    h = complex(out[0], out[1])
+    return (h, float(out[2])) if info else h
+
+
+def lhaf_bruteforce(a) -> complex:
+    """lhaf(a) as the sum over matchings with loops (the diagonal entries are
+    the loop weights), Eq. (loop_hafnian); a symmetric, size <= 14."""
+    a = _c128(a)
+    N = a.shape[0]
+    out = np.zeros(3)
+    _check(_load().oracle_lhaf_bruteforce(_dptr(a), N, _dptr(out)), "lhaf_bruteforce")
+    return complex(out[0], out[1])
+
+
+def lhaf_grouped(b, gamma, r=None, info: bool = False):
+    """Loop hafnian of filldiag(b repeated by r, gamma repeated by r) by the
+    grouped sign-vector formula in double-double."""
+    b = _c128(b)
+    k = b.shape[0]
+    g = _c128(gamma)
+    r = _i32(np.ones(k) if r is None else r)
+    out = np.zeros(3)
+    _check(_load().oracle_lhaf_grouped(_dptr(b), _dptr(g), k, _iptr(r), _dptr(out)),
+           "lhaf_grouped")
     h = complex(out[0], out[1])
     return (h, float(out[2])) if info else h
 

@@ -949,3 +949,171 @@ int oracle_haf_grouped(const double *b, int k, const int *r, double *out)
     out[2] = sumabs * scale;
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* loop hafnian, Eq. (loop_hafnian)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Sum over matchings with loops: the lowest unused index either takes its
+ * loop (weight a_pp) or is paired with every later unused index in turn. */
+static void lhaf_rec(const double *a, int N, int *used, cd_t prod, dd_t *acc_re, dd_t *acc_im,
+                     double *sumabs)
+{
+    int p = 0, q;
+    cd_t x, np;
+    while (p < N && used[p])
+        p++;
+    if (p == N) {
+        *acc_re = dd_add(*acc_re, dd_from(prod.re));
+        *acc_im = dd_add(*acc_im, dd_from(prod.im));
+        *sumabs += hypot(prod.re, prod.im);
+        return;
+    }
+    used[p] = 1;
+    x.re = a[2 * (p * N + p)];
+    x.im = a[2 * (p * N + p) + 1];
+    np = cd_mul(prod, x);
+    lhaf_rec(a, N, used, np, acc_re, acc_im, sumabs);
+    for (q = p + 1; q < N; q++) {
+        if (used[q])
+            continue;
+        used[q] = 1;
+        x.re = a[2 * (p * N + q)];
+        x.im = a[2 * (p * N + q) + 1];
+        np = cd_mul(prod, x);
+        lhaf_rec(a, N, used, np, acc_re, acc_im, sumabs);
+        used[q] = 0;
+    }
+    used[p] = 0;
+}
+
+/* a: N x N complex symmetric (upper triangle and diagonal read), N <= 14, any
+ * parity.  out[0..1] = lhaf(a), out[2] = sum |term|.  Size 0 gives 1. */
+int oracle_lhaf_bruteforce(const double *a, int N, double *out)
+{
+    int used[16] = {0};
+    dd_t re = dd_from(0.0), im = dd_from(0.0);
+    double sumabs = 0.0;
+    cd_t one = {1.0, 0.0};
+    if (N < 0 || N > 14 || out == NULL || (N > 0 && a == NULL))
+        return ORC_ERR_ARG;
+    lhaf_rec(a, N, used, one, &re, &im, &sumabs);
+    out[0] = re.hi + re.lo;
+    out[1] = im.hi + im.lo;
+    out[2] = sumabs;
+    return ORC_OK;
+}
+
+/* Loop hafnian of filldiag(A_r, gamma_r): base index i repeated r_i times in
+ * rows and columns of the k x k symmetric b, the loop weight of every copy of
+ * i being gamma_i (Eq. (loop_hafnian) with the filldiag of the displaced
+ * detection probability).  Grouped sign-vector formula
+ *   lhaf = 1 / 2^{N-1} sum_g (-1)^{sum g} C(r_f - 1, g_f) prod_{i != f} C(r_i, g_i)
+ *            sum_{j=0}^{N/2} q(g)^j l(g)^{N-2j} / (j! (N-2j)!),
+ *   q(g) = 1/2 (x^T b x - sum_i r_i b_ii),  l(g) = gamma^T x,  x_i = r_i - 2 g_i:
+ * the coefficient of the product of all N signs in exp(q + l) counts every
+ * matching with loops once, the mean over sign vectors extracts it, and the
+ * summand is even under flipping every sign, so one copy's sign is fixed.
+ * Every q, l and term from scratch in double-double.
+ * out[0..1] = lhaf, out[2] = sum |term| / 2^{N-1}. */
+int oracle_lhaf_grouped(const double *b, const double *gamma, int k, const int *r, double *out)
+{
+    int i, j, N = 0, f = -1, kd[64];
+    int64_t T = 1, rank;
+    dd_t acc_re = dd_from(0.0), acc_im = dd_from(0.0);
+    double sumabs = 0.0, scale;
+    cd_t dsum;
+    if (k < 0 || k > 64 || out == NULL || (k > 0 && (b == NULL || r == NULL || gamma == NULL)))
+        return ORC_ERR_ARG;
+    for (i = 0; i < k; i++) {
+        if (r[i] < 0)
+            return ORC_ERR_ARG;
+        N += r[i];
+        if (f < 0 && r[i] > 0)
+            f = i;
+    }
+    if (N == 0) {
+        out[0] = 1.0;
+        out[1] = 0.0;
+        out[2] = 1.0;
+        return ORC_OK;
+    }
+    if (N > 62)
+        return ORC_ERR_TOO_LARGE;
+    for (i = 0; i < k; i++) {
+        int64_t rad = (i == f) ? r[i] : r[i] + 1;
+        if (rad < 1)
+            rad = 1;
+        if (T > ((int64_t)1 << 62) / rad)
+            return ORC_ERR_TOO_LARGE;
+        T *= rad;
+    }
+    dsum.re = 0.0;
+    dsum.im = 0.0;
+    for (i = 0; i < k; i++) {
+        dsum.re += r[i] * b[2 * (i * k + i)];
+        dsum.im += r[i] * b[2 * (i * k + i) + 1];
+    }
+    for (rank = 0; rank < T; rank++) {
+        int64_t rem = rank;
+        int gsum = 0;
+        double w = 1.0;
+        cdd_t xbx, q, l, term, qp;
+        for (i = 0; i < k; i++) {
+            int rad = (i == f) ? r[i] : r[i] + 1;
+            if (rad < 1)
+                rad = 1;
+            kd[i] = (int)(rem % rad);
+            rem /= rad;
+            gsum += kd[i];
+            w *= (i == f) ? binom(r[i] - 1, kd[i]) : binom(r[i], kd[i]);
+        }
+        if (gsum & 1)
+            w = -w;
+        xbx.re = dd_from(0.0);
+        xbx.im = dd_from(0.0);
+        l.re = dd_from(0.0);
+        l.im = dd_from(0.0);
+        for (i = 0; i < k; i++) {
+            double xi = (double)(r[i] - 2 * kd[i]);
+            l.re = dd_add(l.re, dd_mul(dd_from(xi), dd_from(gamma[2 * i])));
+            l.im = dd_add(l.im, dd_mul(dd_from(xi), dd_from(gamma[2 * i + 1])));
+            for (j = 0; j < k; j++) {
+                dd_t c = dd_from(xi * (double)(r[j] - 2 * kd[j]));
+                xbx.re = dd_add(xbx.re, dd_mul(c, dd_from(b[2 * (i * k + j)])));
+                xbx.im = dd_add(xbx.im, dd_mul(c, dd_from(b[2 * (i * k + j) + 1])));
+            }
+        }
+        q.re = dd_mul(dd_add(xbx.re, dd_from(-dsum.re)), dd_from(0.5));
+        q.im = dd_mul(dd_add(xbx.im, dd_from(-dsum.im)), dd_from(0.5));
+        /* sum_j q^j l^{N-2j} / (j! (N-2j)!) */
+        term.re = dd_from(0.0);
+        term.im = dd_from(0.0);
+        qp.re = dd_from(1.0);
+        qp.im = dd_from(0.0);
+        for (j = 0; 2 * j <= N; j++) {
+            cdd_t lp, t;
+            int e;
+            lp.re = dd_from(1.0);
+            lp.im = dd_from(0.0);
+            for (e = 0; e < N - 2 * j; e++)
+                lp = cdd_mul(lp, l);
+            t = cdd_mul(qp, lp);
+            t.re = dd_mul(t.re, dd_from(1.0 / (factorial(j) * factorial(N - 2 * j))));
+            t.im = dd_mul(t.im, dd_from(1.0 / (factorial(j) * factorial(N - 2 * j))));
+            term.re = dd_add(term.re, t.re);
+            term.im = dd_add(term.im, t.im);
+            qp = cdd_mul(qp, q);
+        }
+        term.re = dd_mul(term.re, dd_from(w));
+        term.im = dd_mul(term.im, dd_from(w));
+        acc_re = dd_add(acc_re, term.re);
+        acc_im = dd_add(acc_im, term.im);
+        sumabs += hypot(term.re.hi, term.im.hi);
+    }
+    scale = ldexp(1.0, -(N - 1));
+    out[0] = (acc_re.hi + acc_re.lo) * scale;
+    out[1] = (acc_im.hi + acc_im.lo) * scale;
+    out[2] = sumabs * scale;
+    return ORC_OK;
+}

@@ -100,3 +100,109 @@ def test_odd_size_is_zero():
     assert O.haf_grouped(sym(3), [1, 1, 1]) == 0
     with pytest.raises(ValueError):
         O.haf_bruteforce(np.ones((3, 3)))
+
+
+# ---------------------------------------------------------------- loop hafnian
+
+def telephone(N):
+    """Number of involutions of N elements (matchings with loops of K_N)."""
+    t = [1, 1]
+    for m in range(2, N + 1):
+        t.append(t[-1] + (m - 1) * t[-2])
+    return t[N]
+
+
+def filldiag(B, gamma, r):
+    A = expand(B, r)
+    np.fill_diagonal(A, np.repeat(np.asarray(gamma), r))
+    return A
+
+
+def exact_lhaf(a):
+    """Exact loop hafnian on Gaussian integers (loops from the diagonal)."""
+    re, im, E = to_gaussian_ints(a)
+    N = re.shape[0]
+
+    def mul(x, y):
+        return (x[0] * y[0] - x[1] * y[1], x[0] * y[1] + x[1] * y[0])
+
+    def rec(rem):
+        # returns (value, number of loops used is folded into the scale below)
+        if not rem:
+            return {0: (1, 0)}
+        p, rest = rem[0], rem[1:]
+        out = {}
+        for loops, v in rec(rest).items():  # p takes its loop
+            w = mul((re[p, p], im[p, p]), v)
+            o = out.get(loops + 1, (0, 0))
+            out[loops + 1] = (o[0] + w[0], o[1] + w[1])
+        for idx, q in enumerate(rest):
+            for loops, v in rec(rest[:idx] + rest[idx + 1:]).items():
+                w = mul((re[p, q], im[p, q]), v)
+                o = out.get(loops, (0, 0))
+                out[loops] = (o[0] + w[0], o[1] + w[1])
+        return out
+
+    tot_re, tot_im = Fraction(0), Fraction(0)
+    for loops, v in rec(tuple(range(N))).items():
+        factors = loops + (N - loops) // 2  # entries multiplied in each product
+        scale = 1 << (E * factors)
+        tot_re += Fraction(v[0], scale)
+        tot_im += Fraction(v[1], scale)
+    return complex(float(tot_re), float(tot_im))
+
+
+@pytest.mark.parametrize("N", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+def test_lhaf_all_ones_counts_involutions(N):
+    want = telephone(N)
+    assert O.lhaf_bruteforce(np.ones((N, N))) == want
+    if N:
+        assert abs(O.lhaf_grouped([[1.0]], [1.0], [N]) - want) <= 1e-12 * want
+        assert abs(O.lhaf_grouped(np.ones((N, N)), np.ones(N)) - want) <= 1e-12 * want
+
+
+def test_lhaf_reduces_to_haf_and_to_diagonal_product():
+    B = sym(6)
+    np.fill_diagonal(B, 0)
+    assert abs(O.lhaf_bruteforce(B) - O.haf_bruteforce(B)) <= 1e-14 * abs(O.haf_bruteforce(B))
+    g0 = np.zeros(6)
+    assert abs(O.lhaf_grouped(B, g0) - O.haf_bruteforce(B)) <= 1e-12 * abs(O.haf_bruteforce(B))
+    d = RNG.standard_normal(5) + 1j * RNG.standard_normal(5)
+    D = np.diag(d)
+    assert abs(O.lhaf_bruteforce(D) - np.prod(d)) <= 1e-14
+    assert abs(O.lhaf_grouped(np.zeros((5, 5)), d) - np.prod(d)) <= 1e-13
+
+
+def test_lhaf_hand_value_three():
+    # 3 x 3: three loops, or one pair and the remaining loop
+    a = np.array([[2.0, 3, 5], [3, 7, 11], [5, 11, 13]])
+    want = 2 * 7 * 13 + 3 * 13 + 5 * 7 + 11 * 2
+    assert O.lhaf_bruteforce(a) == want
+    assert abs(O.lhaf_grouped(a, np.diag(a)) - want) <= 1e-12 * want
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 8, 11])
+def test_lhaf_single_index_closed_form(N):
+    # one index repeated N times: sum_j C(N, 2j) (2j-1)!! b^j c^{N-2j}
+    b, c = 0.7 - 0.2j, -0.4 + 0.9j
+    want = sum(math.comb(N, 2 * j) * double_factorial(2 * j - 1) * b ** j * c ** (N - 2 * j)
+               for j in range(N // 2 + 1))
+    got = O.lhaf_grouped([[b]], [c], [N])
+    assert abs(got - want) <= 1e-13 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("N", [3, 4, 6, 7])
+def test_lhaf_bruteforce_matches_exact(N):
+    a = sym(N)
+    ref = exact_lhaf(a)
+    assert abs(O.lhaf_bruteforce(a) - ref) <= 1e-13 * max(1, abs(ref))
+
+
+@pytest.mark.parametrize("r", [[1, 1, 1], [2, 1], [2, 2], [3, 1, 1], [1, 2, 2, 2], [5],
+                               [2, 2, 2, 1], [1, 0, 3]])
+def test_lhaf_grouped_matches_definition_on_filled_matrix(r):
+    B = sym(len(r))
+    gamma = RNG.standard_normal(len(r)) + 1j * RNG.standard_normal(len(r))
+    ref = O.lhaf_bruteforce(filldiag(B, gamma, r))
+    got, scale = O.lhaf_grouped(B, gamma, r, info=True)
+    assert abs(got - ref) <= 1e-13 * max(abs(ref), scale)
