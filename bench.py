@@ -447,6 +447,20 @@ def extra_measurements(args, dev, stream, flush):
         ms = timed(lambda: api.permanent_batched(dbk, plank, out=outk, stream=stream), 5)
         sweep[str(k)] = {"ms": ms, "terms": stk["terms"], "terms_per_s": stk["terms"] / ms * 1e3}
     res["paper_repeated_2x"] = sweep
+    # the paper's repeated hafnian / loop hafnian benchmark shape (Figs.
+    # hafnian, loop_hafnian): k x k GBS matrix, every index repeated twice
+    # (N = 2k); one synchronous call each (planning and upload included)
+    for loop in (False, True):
+        hs = {}
+        for k in range(4, 21, 2):
+            B, r, g = W.paper_repeated_hafnian(k, loop=loop)
+            Bd = torch.from_numpy(B.reshape(-1)).to(dev)
+            gd = torch.from_numpy(g).to(dev) if loop else None
+            terms = 2 * 3 ** (k - 1)
+            ms = timed(lambda: api.hafnian_repeated(Bd, [0], [k], r, [0], gamma=gd,
+                                                    stream=stream), 3)
+            hs[str(k)] = {"N": 2 * k, "ms": ms, "terms": terms, "terms_per_s": terms / ms * 1e3}
+        res["paper_loop_hafnian_2x" if loop else "paper_hafnian_2x"] = hs
     # Algorithm A sampler (one batched launch per photon over all samples),
     # m = 16 Haar interferometer, 8 photons, 2000 samples
     Us = torch.from_numpy(W.haar_unitary(16, W.rng_for(7))).to(dev)

@@ -224,6 +224,44 @@ int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c128* W, int
 int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_occ, int64_t nsamples,
                  const int32_t* col_order, const double* uniforms, int32_t* samples, void* stream);
 
+/* Hafnians with repeated indices (Sec. 4.1, Eq. (haf_def); the paper's
+ * hafnian benchmark repeats every index twice).  Item b is the hafnian of the
+ * N x N matrix that repeats base index i of the symmetric k[b] x k[b] base
+ * matrix rep[rep_off[b] + i] times in both rows and columns, N = sum of the
+ * repetitions.  Evaluated by the sign-vector (Glynn-type) formula
+ *   haf = 1/(n! 2^{N-1}) sum_g (-1)^{|g|} prod_i C(top_i, g_i) q(g)^n,
+ *   q(g) = 1/2 (x^T B x - sum_i r_i B_ii),  x_i = r_i - 2 g_i,  n = N/2,
+ * one copy of the least repeated index fixed to +, over a mixed-radix Gray
+ * code with O(k) work per term and double-double accumulation.  Odd N gives
+ * 0, N = 0 gives 1.
+ * mats: device, packed row-major complex bases at element offsets
+ * mat_off[b] (host, int64); k, rep, rep_off: host; only the upper triangle
+ * and diagonal matter for a symmetric base (the kernel reads both halves, so
+ * pass a symmetric matrix).  out: device, batch complex.  N <= PQ_MAX_N,
+ * k <= PQ_MAX_DIM.  Allocates its workspace and synchronises `stream`.
+ * Errors: PQ_ERR_ARG (null, negative sizes or repetitions),
+ * PQ_ERR_UNSUPPORTED (N or term count too large), PQ_ERR_NOMEM, PQ_ERR_CUDA. */
+int pq_hafnian_repeated(const pq_c128* mats, const int64_t* mat_off, const int32_t* k,
+                        const int32_t* rep, const int64_t* rep_off, int64_t batch, pq_c128* out,
+                        void* stream);
+
+/* Loop hafnians with repeated indices (Eq. (loop_hafnian), with the filldiag
+ * of the displaced Gaussian detection probability in Appendix A: every copy
+ * of base index i gets the loop weight gamma_i on the diagonal).  Item b is
+ * lhaf(filldiag(A_r, gamma_r)), A_r repeating index i of the k[b] x k[b] base
+ * rep[rep_off[b] + i] times.  Glynn-type formula
+ *   lhaf = 1/2^{N-1} sum_g (-1)^{|g|} prod_i C(top_i, g_i)
+ *          sum_{j <= N/2} q(g)^j l(g)^{N-2j} / (j! (N-2j)!),   l(g) = gamma^T x,
+ * q, x, the digits and the Gray walk as for pq_hafnian_repeated; any N >= 0
+ * (N = 0 gives 1).  gamma: device, complex, packed like rep (element
+ * rep_off[b] + i is the loop weight of base index i of item b); the base
+ * diagonal B_ii is still the weight of a pair of two copies of index i.
+ * Other arguments, allocation, synchronisation and errors as for
+ * pq_hafnian_repeated (PQ_ERR_ARG also for gamma == NULL with batch > 0). */
+int pq_loop_hafnian_repeated(const pq_c128* mats, const pq_c128* gamma, const int64_t* mat_off,
+                             const int32_t* k, const int32_t* rep, const int64_t* rep_off,
+                             int64_t batch, pq_c128* out, void* stream);
+
 /* Times trial launches of the plan's batched kernel for each size class on
  * the given data and stores the fastest chunk length per class in the plan
  * (and in the process-wide tuning table used by later plans).  Synchronises

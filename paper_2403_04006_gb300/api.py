@@ -153,7 +153,8 @@ def permanent_backward(db: DeviceBatch, grad_out: torch.Tensor, plan: Plan | Non
                        mats: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     m = db.mats if mats is None else mats
     grad = torch.empty_like(m)
-    _pq.pq_permanent_backward(db.c_struct(mats), _ptr(grad_out.contiguous()), _ptr(grad),
+    go = grad_out.contiguous()  # held until the call returns
+    _pq.pq_permanent_backward(db.c_struct(mats), _ptr(go), _ptr(grad),
                               plan.handle if plan else None, _stream_handle(stream))
     return grad
 
@@ -172,8 +173,9 @@ def bs_probs(U: torch.Tensor, s: torch.Tensor, t: torch.Tensor, plan: Plan | Non
 def bs_probs_backward(U, s, t, grad_probs, amps, plan: Plan | None = None, stream=None):
     m = U.shape[0]
     gU = torch.empty_like(U)
+    gp = grad_probs.contiguous()  # held until the call returns
     _pq.pq_bs_probs_backward(_ptr(U), m, _ptr(s), _ptr(t), t.shape[0],
-                             _ptr(grad_probs.contiguous()), _ptr(amps), _ptr(gU),
+                             _ptr(gp), _ptr(amps), _ptr(gU),
                              plan.handle if plan else None, _stream_handle(stream))
     return gU
 
@@ -187,7 +189,8 @@ def clements_forward(theta: torch.Tensor, phi: torch.Tensor, m: int, stream=None
 def clements_backward(theta, phi, m, U, grad_U, stream=None):
     gt = torch.empty_like(theta)
     gp = torch.empty_like(phi)
-    _pq.pq_clements_backward(_ptr(theta), _ptr(phi), m, _ptr(U), _ptr(grad_U.contiguous()),
+    gUc = grad_U.contiguous()  # held until the call returns
+    _pq.pq_clements_backward(_ptr(theta), _ptr(phi), m, _ptr(U), _ptr(gUc),
                              _ptr(gt), _ptr(gp), _stream_handle(stream))
     return gt, gp
 
@@ -262,7 +265,10 @@ def bs_probs_lossy(V: torch.Tensor, eta: torch.Tensor, W: torch.Tensor, s, t,
     t = np.atleast_2d(np.asarray(t, dtype=np.int32))
     m = V.shape[0]
     probs = torch.empty(t.shape[0], dtype=torch.float64, device=V.device)
-    _pq.pq_bs_probs_lossy(_ptr(V.contiguous()), _ptr(eta.contiguous()), _ptr(W.contiguous()), m,
+    # Contiguous copies are bound to names so that none is freed (and its
+    # block reused by the next copy) before the call reads it.
+    Vc, etac, Wc = V.contiguous(), eta.contiguous(), W.contiguous()
+    _pq.pq_bs_probs_lossy(_ptr(Vc), _ptr(etac), _ptr(Wc), m,
                           np.asarray(s), t, _ptr(probs), _stream_handle(stream))
     return probs
 
@@ -271,5 +277,22 @@ def bs_sample(U: torch.Tensor, s, col_order, uniforms, stream=None) -> np.ndarra
     """Boson-sampling outputs by Algorithm A (pq_bs_sample): U on the GPU,
     input occupation s, and the run's random column orders and uniforms
     (host arrays, nsamples x n).  Returns nsamples x m occupations."""
-    return _pq.pq_bs_sample(_ptr(U.contiguous()), U.shape[0], np.asarray(s), col_order,
+    Uc = U.contiguous()
+    return _pq.pq_bs_sample(_ptr(Uc), U.shape[0], np.asarray(s), col_order,
                             uniforms, _stream_handle(stream))
+
+
+def hafnian_repeated(mats: torch.Tensor, mat_off, k, rep, rep_off, gamma: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """Hafnians of symmetric bases with repeated indices (pq_hafnian_repeated),
+    or loop hafnians with loop weights ``gamma`` (pq_loop_hafnian_repeated;
+    packed like ``rep``): ``mats`` packed complex128 on the GPU, the offsets,
+    sizes and repetitions host arrays.  Returns one complex128 per item."""
+    mc = mats.contiguous()
+    gc = None if gamma is None else gamma.contiguous()
+    nb = len(k)
+    out = torch.empty(nb, dtype=torch.complex128, device=mats.device)
+    _pq.pq_hafnian_repeated(_ptr(mc), np.asarray(mat_off), np.asarray(k), np.asarray(rep),
+                            np.asarray(rep_off), _ptr(out) if nb else None,
+                            _stream_handle(stream), gamma_ptr=_ptr(gc), loop=gc is not None)
+    return out

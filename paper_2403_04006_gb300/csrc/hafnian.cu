@@ -1,0 +1,574 @@
+// hafnian.cu -- hafnians and loop hafnians of symmetric matrices with
+// repeated indices (Sec. 4.1, Eq. (haf_def), Eq. (loop_hafnian), Figs.
+// hafnian and loop_hafnian with (2, ..., 2) repetitions), on the same
+// warp-uniform mixed-radix Gray walk and double-double accumulation as the
+// permanent.
+//
+// Glynn-type formulas (a reading: the paper names the Glynn-type strategy but
+// prints no formula).  For a sign vector d of the N expanded indices, the
+// coefficient of d_1 ... d_N in exp(Q(d) + Lin(d)), Q = sum_{p<q} A_pq d_p d_q,
+// Lin = sum_p A_pp d_p, counts every matching with loops once, and the mean of
+// (prod d) times a polynomial in d is exactly that coefficient.  Without loops
+// only Q^n / n! (N = 2n) has degree N.  With base index i repeated r_i times
+// and g_i of its copies negative, x_i = r_i - 2 g_i and, B the base matrix and
+// gamma the loop weights,
+//   q(g) = 1/2 (x^T B x - sum_i r_i B_ii),   l(g) = gamma^T x,
+//   haf  = 1 / (n! 2^{N-1}) sum_g s(g) q^n,
+//   lhaf = 1 / 2^{N-1} sum_g s(g) sum_{j <= N/2} q^j l^{N-2j} / (j! (N-2j)!),
+//   s(g) = (-1)^{sum g} prod_i C(top_i, g_i),
+// one copy of the least repeated index keeping a + sign (top = r - 1 there;
+// the summand is even under flipping every sign).  A Gray step changes one
+// x_r by D = -+2:  q += D y_r + 2 B_rr with y = B x, then y_j += D B_jr and
+// l += D gamma_r: O(k) work per term.  q^n is taken by repeated squaring; the
+// loop polynomial by a homogeneous Horner scheme in q and l^2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "../../include/pq.h"
+#include "pq_device.cuh"
+#include "pq_kernels.h"
+
+namespace pqi {
+
+constexpr int kHafMaxHalf = PQ_MAX_N / 2;  // Horner coefficients j = 0 .. N/2
+
+// Per (loop) hafnian: k kept base indices, digits as for the permanent.
+struct alignas(16) HafDesc {
+    int64_t T, nchunks, L, src_off, gam_off;
+    int32_t k, n, N, ld;   // kept indices, N/2, expanded size, source row stride
+    int32_t meta;          // ridx[k], rmul[k], drow[nd], drad[nd], dtop[nd]
+    int32_t ndig, J, ntasks, slot0;
+    int32_t weighted, trivial;  // trivial: result = value (0 for odd N, 1 for N = 0)
+    double value;               // final multiplier (or the trivial result)
+};
+
+struct HafArgs {
+    const HafDesc* desc;
+    const int32_t* meta;
+    const Task* tasks;
+    int64_t ntasks;
+    const double2* src;
+    const double2* gamma;  // loop weights (loop hafnian only)
+    double2* out;
+    double* partials;
+    int32_t* counters;
+};
+
+// Shared memory of one warp: M (k x k), y0 = B r (k), gamma (k),
+// y (k x 32, lane-major), Horner coefficients, low-digit rows.
+__host__ __device__ inline int haf_warp_smem_bytes(int kmax)
+{
+    int bytes = (kmax * kmax + 2 * kmax + 32 * kmax) * 16 + (kHafMaxHalf + 1) * 8 + 16 * 4;
+    return (bytes + 15) & ~15;
+}
+
+// p = q^n, n >= 1 (warp-uniform n)
+__device__ __forceinline__ double2 cpow_n(double2 q, int n)
+{
+    double2 p = q;
+    int top = 31 - __clz(n);
+#pragma unroll 1
+    for (int b = top - 1; b >= 0; --b) {
+        p = cmul(p, p);
+        if ((n >> b) & 1)
+            p = cmul(p, q);
+    }
+    return p;
+}
+
+// sum_{j=0}^{N/2} c_j q^j l^{N-2j} by h <- h q + c_j (l^2)^{N/2-j}
+__device__ __forceinline__ double2 loop_poly(double2 q, double2 l, int N, const double* cj)
+{
+    const int J = N >> 1;
+    const double2 s = cmul(l, l);
+    double2 h = make_double2(cj[J], 0.0);
+    double2 w = make_double2(1.0, 0.0);
+#pragma unroll 1
+    for (int j = J - 1; j >= 0; --j) {
+        w = cmul(w, s);
+        h = cmul(h, q);
+        h.x = __fma_rn(cj[j], w.x, h.x);
+        h.y = __fma_rn(cj[j], w.y, h.y);
+    }
+    if (N & 1)
+        h = cmul(h, l);
+    return h;
+}
+
+template <bool LOOP>
+__device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, int kmax, int& staged,
+                         int lane)
+{
+    const HafDesc D = a.desc[t.perm];
+    const int k = D.k, J = D.J, nd = D.ndig;
+    double2* M = reinterpret_cast<double2*>(raw);
+    double2* y0 = M + kmax * kmax;
+    double2* gam = y0 + kmax;
+    double2* Y = gam + kmax;
+    double* cj = reinterpret_cast<double*>(Y + 32 * kmax);
+    int32_t* lowrow = reinterpret_cast<int32_t*>(cj + kHafMaxHalf + 1);
+    const int32_t* ridx = a.meta + D.meta;
+    const int32_t* rmul = ridx + k;
+    const int32_t* drow = rmul + k;
+    const int32_t* drad = drow + nd;
+    const int32_t* dtop = drad + nd;
+    dd2 res = {0.0, 0.0, 0.0, 0.0};
+
+    if (!D.trivial) {
+        if (staged != t.perm) {
+            __syncwarp();
+            for (int e = lane; e < k * k; e += kWarp) {
+                const int i = e / k, j = e - i * k;
+                M[e] = a.src[D.src_off + (int64_t)ridx[i] * D.ld + ridx[j]];
+            }
+            for (int d = lane; d < J; d += kWarp)
+                lowrow[d] = drow[d];
+            if (LOOP) {
+                for (int i = lane; i < k; i += kWarp)
+                    gam[i] = a.gamma[D.gam_off + ridx[i]];
+                for (int j = lane; j <= D.N / 2; j += kWarp) {  // 1 / (j! (N-2j)!)
+                    double f = 1.0;
+                    for (int i = 2; i <= j; ++i)
+                        f *= (double)i;
+                    for (int i = 2; i <= D.N - 2 * j; ++i)
+                        f *= (double)i;
+                    cj[j] = 1.0 / f;
+                }
+            }
+            __syncwarp();
+            for (int j = lane; j < k; j += kWarp) {  // y0 = B r
+                double2 s = make_double2(0.0, 0.0);
+                for (int i = 0; i < k; ++i) {
+                    const double r = (double)rmul[i];
+                    s.x = __fma_rn(r, M[j * k + i].x, s.x);
+                    s.y = __fma_rn(r, M[j * k + i].y, s.y);
+                }
+                y0[j] = s;
+            }
+            __syncwarp();
+            staged = t.perm;
+        }
+        const int64_t chunk0 = (int64_t)t.part * kWarp;
+        const bool active = chunk0 + lane < D.nchunks;
+        int64_t c = active ? (chunk0 + lane) : 0;
+        const int64_t c_first = c;
+        double2* y = Y + lane;
+#pragma unroll 1
+        for (int j = 0; j < k; ++j)
+            y[j * 32] = y0[j];
+        // High digits of this lane's chunk: x_row = r_row - 2 g.  y = B x is
+        // finished before x^T y is formed in a second pass over the digits.
+        uint64_t whigh_u = 1;
+        int gpar = 0;
+#pragma unroll 1
+        for (int d = J; d < nd; ++d) {
+            const int rad = drad[d];
+            const int g = (int)(c % rad);
+            c /= rad;
+            if (!g)
+                continue;
+            const int row = drow[d];
+            const double coef = (double)(-2 * g);
+#pragma unroll 1
+            for (int j = 0; j < k; ++j) {
+                const double2 b = M[j * k + row];
+                double2 v = y[j * 32];
+                v.x = __fma_rn(coef, b.x, v.x);
+                v.y = __fma_rn(coef, b.y, v.y);
+                y[j * 32] = v;
+            }
+            whigh_u *= binom_u64(dtop[d], g);
+            gpar += g;
+        }
+        // q = 1/2 (x^T y - sum_i r_i B_ii) and l = gamma^T x, low digits at 0
+        double2 q = make_double2(0.0, 0.0), l = make_double2(0.0, 0.0);
+#pragma unroll 1
+        for (int i = 0; i < k; ++i) {
+            const double2 v = y[i * 32];
+            const double2 bii = M[i * k + i];
+            const double r = (double)rmul[i];
+            q.x = __fma_rn(r, __dsub_rn(v.x, bii.x), q.x);
+            q.y = __fma_rn(r, __dsub_rn(v.y, bii.y), q.y);
+            if (LOOP) {
+                l.x = __fma_rn(r, gam[i].x, l.x);
+                l.y = __fma_rn(r, gam[i].y, l.y);
+            }
+        }
+        c = c_first;
+#pragma unroll 1
+        for (int d = J; d < nd; ++d) {
+            const int rad = drad[d];
+            const int g = (int)(c % rad);
+            c /= rad;
+            if (!g)
+                continue;
+            const int row = drow[d];
+            const double2 v = y[row * 32];
+            const double coef = (double)(-2 * g);
+            q.x = __fma_rn(coef, v.x, q.x);
+            q.y = __fma_rn(coef, v.y, q.y);
+            if (LOOP) {
+                l.x = __fma_rn(coef, gam[row].x, l.x);
+                l.y = __fma_rn(coef, gam[row].y, l.y);
+            }
+        }
+        q.x *= 0.5;
+        q.y *= 0.5;
+        double whigh = active ? (double)whigh_u : 0.0;
+        if (gpar & 1)
+            whigh = -whigh;
+
+        LowWalk wk;
+        wk.v = 0;
+        wk.g = 0;
+        wk.dir = 0;
+        wk.radm1 = 0;
+        wk.topp = 0;
+        for (int d = 0; d < J; ++d) {
+            wk.radm1 |= uint64_t(drad[d] - 1) << (4 * d);
+            wk.topp |= uint64_t(dtop[d]) << (4 * d);
+        }
+        const bool weighted = D.weighted != 0;
+        const int n = D.n, N = D.N;
+        double wlow = 1.0;
+        double2 acc = make_double2(0.0, 0.0);
+        double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+        const int64_t L = D.L;
+        int blk = 0;
+#pragma unroll 1
+        for (int64_t s = 0; s < L; ++s) {
+            const double2 p = LOOP ? loop_poly(q, l, N, cj) : cpow_n(q, n);
+            const double ws = (s & 1) ? -wlow : wlow;
+            acc.x = __fma_rn(ws, p.x, acc.x);
+            acc.y = __fma_rn(ws, p.y, acc.y);
+            if (s + 1 < L) {
+                int up;
+                const int d = low_step(wk, up);
+                const int row = lowrow[d];
+                const double delta = up > 0 ? -2.0 : 2.0;
+                const double2 yr = y[row * 32];
+                const double2 brr = M[row * k + row];
+                q.x = __fma_rn(delta, yr.x, q.x);
+                q.y = __fma_rn(delta, yr.y, q.y);
+                q.x = __fma_rn(2.0, brr.x, q.x);
+                q.y = __fma_rn(2.0, brr.y, q.y);
+                if (LOOP) {
+                    l.x = __fma_rn(delta, gam[row].x, l.x);
+                    l.y = __fma_rn(delta, gam[row].y, l.y);
+                }
+#pragma unroll 1
+                for (int j = 0; j < k; ++j) {
+                    const double2 b = M[j * k + row];
+                    double2 v = y[j * 32];
+                    v.x = __fma_rn(delta, b.x, v.x);
+                    v.y = __fma_rn(delta, b.y, v.y);
+                    y[j * 32] = v;
+                }
+                if (weighted && ((wk.radm1 >> (4 * d)) & 15u) > 1u)
+                    wlow = (double)low_weight(wk, J);
+            }
+            if (++blk == 16) {
+                blk = 0;
+                dd_acc(rh, rl, acc.x);
+                dd_acc(ih, il, acc.y);
+                acc = make_double2(0.0, 0.0);
+            }
+        }
+        dd_acc(rh, rl, acc.x);
+        dd_acc(ih, il, acc.y);
+        fast_two_sum(rh, rl, rh, rl);
+        fast_two_sum(ih, il, ih, il);
+        dd_mul_d(rh, rl, whigh);
+        dd_mul_d(ih, il, whigh);
+        res.rh = rh;
+        res.rl = rl;
+        res.ih = ih;
+        res.il = il;
+        res = warp_sum_dd2(res);
+    }
+
+    auto finish = [&](dd2 v) {
+        double2 o;
+        if (D.trivial) {
+            o = make_double2(D.value, 0.0);
+        } else {
+            double h, e;
+            fast_two_sum(v.rh, v.rl, h, e);
+            o.x = scalbn(h + e, 1 - D.N) * D.value;
+            fast_two_sum(v.ih, v.il, h, e);
+            o.y = scalbn(h + e, 1 - D.N) * D.value;
+        }
+        a.out[t.perm] = o;
+    };
+    if (D.ntasks <= 1) {
+        if (lane == 0)
+            finish(res);
+        return;
+    }
+    // Several tasks: partials in task order; the last warp to finish sums them
+    // in a fixed order (no waiting on other warps).
+    int last = 0;
+    if (lane == 0) {
+        double* pp = a.partials + 4 * (int64_t)(D.slot0 + t.part);
+        pp[0] = res.rh;
+        pp[1] = res.rl;
+        pp[2] = res.ih;
+        pp[3] = res.il;
+        __threadfence();
+        last = (atomicAdd(a.counters + 1 + t.perm, 1) == D.ntasks - 1);
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last)
+        return;
+    __threadfence();
+    dd2 tot = {0.0, 0.0, 0.0, 0.0};
+    for (int p = lane; p < D.ntasks; p += kWarp) {
+        const double* pp = a.partials + 4 * (int64_t)(D.slot0 + p);
+        dd_add(tot.rh, tot.rl, __ldcg(pp + 0), __ldcg(pp + 1));
+        dd_add(tot.ih, tot.il, __ldcg(pp + 2), __ldcg(pp + 3));
+    }
+    tot = warp_sum_dd2(tot);
+    if (lane == 0)
+        finish(tot);
+}
+
+// Persistent: every warp takes tasks from a global queue (counters[0]).
+template <bool LOOP>
+__global__ void __launch_bounds__(256) hafnian_kernel(HafArgs a, int kmax)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* raw = smem_raw + warp * haf_warp_smem_bytes(kmax);
+    int staged = -1;
+    for (;;) {
+        int q = 0;
+        if (lane == 0)
+            q = atomicAdd(a.counters, 1);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= a.ntasks)
+            break;
+        haf_task<LOOP>(a, a.tasks[q], raw, kmax, staged, lane);
+    }
+}
+
+static double factorial_h(int n)
+{
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i)
+        r *= (double)i;
+    return r;
+}
+
+// Plan, upload, run and synchronise; gamma == nullptr selects the hafnian.
+static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32_t* k,
+                        const int32_t* rep, const int64_t* rep_off, const pq_c128* gamma,
+                        int64_t batch, pq_c128* out, void* stream)
+{
+    const bool loop = gamma != nullptr;
+    if (batch < 0 || (batch > 0 && (!mats || !mat_off || !k || !rep || !rep_off || !out)))
+        return report(PQ_ERR_ARG, "null argument or negative batch");
+    if (batch > (int64_t(1) << 30))
+        return report(PQ_ERR_UNSUPPORTED, "batch above 2^30");
+    std::vector<HafDesc> desc(batch);
+    std::vector<int32_t> meta;
+    std::vector<Task> tasks;
+    std::vector<double> cost;
+    int kmax = 1;
+    int32_t slot = 0;
+    for (int64_t b = 0; b < batch; ++b) {
+        HafDesc& D = desc[b];
+        std::memset(&D, 0, sizeof(D));
+        if (k[b] < 0 || k[b] > PQ_MAX_DIM || mat_off[b] < 0 || rep_off[b] < 0)
+            return report(PQ_ERR_ARG, "bad size or offset");
+        const int32_t* r = rep + rep_off[b];
+        std::vector<int32_t> ridx, rm;
+        int N = 0;
+        for (int i = 0; i < k[b]; ++i) {
+            if (r[i] < 0)
+                return report(PQ_ERR_ARG, "negative repetition");
+            if (r[i] > PQ_MAX_N)
+                return report(PQ_ERR_UNSUPPORTED, "expanded size above PQ_MAX_N");
+            if (r[i] > 0) {
+                ridx.push_back(i);
+                rm.push_back(r[i]);
+                N += r[i];
+            }
+        }
+        if (N > PQ_MAX_N)
+            return report(PQ_ERR_UNSUPPORTED, "expanded size above PQ_MAX_N");
+        D.src_off = mat_off[b];
+        D.gam_off = rep_off[b];
+        D.ld = k[b];
+        D.N = N;
+        D.n = N / 2;
+        D.slot0 = slot;
+        if (N == 0 || (!loop && (N & 1))) {
+            D.trivial = 1;
+            D.value = (N == 0) ? 1.0 : 0.0;
+            D.ntasks = 1;
+            tasks.push_back(Task{(int32_t)b, 0});
+            cost.push_back(0.0);
+            slot += 1;
+            continue;
+        }
+        const int kk = (int)ridx.size();
+        kmax = std::max(kmax, kk);
+        D.k = kk;
+        D.value = loop ? 1.0 : 1.0 / factorial_h(N / 2);
+        // Digits: one copy of the least repeated index fixed (radix r_f), the
+        // others radix r_i + 1; ascending radix so that small ones walk inside
+        // a chunk.
+        const int f = (int)(std::min_element(rm.begin(), rm.end()) - rm.begin());
+        struct Dg {
+            int rad, row, top;
+        };
+        std::vector<Dg> dg;
+        int64_t T = 1;
+        for (int i = 0; i < kk; ++i) {
+            const int rad = (i == f) ? rm[i] : rm[i] + 1;
+            if (rad < 2)
+                continue;
+            dg.push_back({rad, i, (i == f) ? rm[i] - 1 : rm[i]});
+            if (T > (int64_t(1) << 62) / rad)
+                return report(PQ_ERR_UNSUPPORTED, "term count above 2^62");
+            T *= rad;
+        }
+        std::stable_sort(dg.begin(), dg.end(), [](const Dg& x, const Dg& y) { return x.rad < y.rad; });
+        D.T = T;
+        D.ndig = (int)dg.size();
+        // Chunk length: at most 1024 terms and at least 32 chunks when T allows.
+        const int64_t target = std::max<int64_t>(1, std::min<int64_t>(T / kWarp, 1024));
+        int J = 0;
+        int64_t L = 1;
+        while (J < D.ndig && J < kMaxLowDigits && dg[J].rad <= kMaxLowRadix &&
+               L * dg[J].rad <= target) {
+            L *= dg[J].rad;
+            ++J;
+        }
+        D.J = J;
+        D.L = L;
+        D.nchunks = T / L;
+        for (int d = 0; d < J; ++d)
+            if (dg[d].rad > 2)
+                D.weighted = 1;
+        const int64_t nt = (D.nchunks + kWarp - 1) / kWarp;
+        if (nt + slot > (int64_t(1) << 30))
+            return report(PQ_ERR_UNSUPPORTED, "too many tasks");
+        D.ntasks = (int32_t)nt;
+        D.meta = (int32_t)meta.size();
+        meta.insert(meta.end(), ridx.begin(), ridx.end());
+        meta.insert(meta.end(), rm.begin(), rm.end());
+        for (const Dg& d : dg)
+            meta.push_back(d.row);
+        for (const Dg& d : dg)
+            meta.push_back(d.rad);
+        for (const Dg& d : dg)
+            meta.push_back(d.top);
+        const double per_term = loop ? (2.0 * kk + 10.0 * (N / 2) + 12.0) : (2.0 * kk + 24.0);
+        for (int64_t q = 0; q < nt; ++q) {
+            tasks.push_back(Task{(int32_t)b, (int32_t)q});
+            cost.push_back((double)L * per_term);
+        }
+        slot += (int32_t)nt;
+    }
+    if (batch == 0)
+        return PQ_OK;
+    // longest task first
+    std::vector<int64_t> order(tasks.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t x, int64_t y) { return cost[x] > cost[y]; });
+    std::vector<Task> sorted(tasks.size());
+    for (size_t q = 0; q < order.size(); ++q)
+        sorted[q] = tasks[order[q]];
+    cudaStream_t st = (cudaStream_t)stream;
+    HafDesc* desc_d = nullptr;
+    int32_t* meta_d = nullptr;
+    Task* tasks_d = nullptr;
+    double* part_d = nullptr;
+    int32_t* cnt_d = nullptr;
+    int rc = PQ_OK;
+    if (cudaMalloc((void**)&desc_d, sizeof(HafDesc) * batch) != cudaSuccess ||
+        cudaMalloc((void**)&meta_d, sizeof(int32_t) * std::max<size_t>(meta.size(), 1)) != cudaSuccess ||
+        cudaMalloc((void**)&tasks_d, sizeof(Task) * sorted.size()) != cudaSuccess ||
+        cudaMalloc((void**)&part_d, sizeof(double) * 4 * std::max<int32_t>(slot, 1)) != cudaSuccess ||
+        cudaMalloc((void**)&cnt_d, sizeof(int32_t) * (batch + 1)) != cudaSuccess)
+        rc = report(PQ_ERR_NOMEM, "hafnian workspace allocation failed");
+    if (rc == PQ_OK &&
+        (cudaMemcpyAsync(desc_d, desc.data(), sizeof(HafDesc) * batch, cudaMemcpyHostToDevice,
+                         st) != cudaSuccess ||
+         (!meta.empty() && cudaMemcpyAsync(meta_d, meta.data(), sizeof(int32_t) * meta.size(),
+                                           cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+         cudaMemcpyAsync(tasks_d, sorted.data(), sizeof(Task) * sorted.size(),
+                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemsetAsync(cnt_d, 0, sizeof(int32_t) * (batch + 1), st) != cudaSuccess))
+        rc = report(PQ_ERR_CUDA, "hafnian upload failed");
+    if (rc == PQ_OK) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_warp = haf_warp_smem_bytes(kmax);
+        int wpb = 8;
+        while (wpb > 1 && wpb * per_warp > 227 * 1024)
+            --wpb;
+        const int bps = std::max(1, std::min(2, (227 * 1024) / (wpb * per_warp)));
+        HafArgs a;
+        a.desc = desc_d;
+        a.meta = meta_d;
+        a.tasks = tasks_d;
+        a.ntasks = (int64_t)sorted.size();
+        a.src = reinterpret_cast<const double2*>(mats);
+        a.gamma = reinterpret_cast<const double2*>(gamma);
+        a.out = reinterpret_cast<double2*>(out);
+        a.partials = part_d;
+        a.counters = cnt_d;
+        const int64_t want_blocks = (a.ntasks + wpb - 1) / wpb;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * bps, want_blocks));
+        cudaError_t e;
+        if (loop) {
+            e = cudaFuncSetAttribute(hafnian_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * per_warp);
+            if (e == cudaSuccess)
+                hafnian_kernel<true><<<blocks, 32 * wpb, wpb * per_warp, st>>>(a, kmax);
+        } else {
+            e = cudaFuncSetAttribute(hafnian_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * per_warp);
+            if (e == cudaSuccess)
+                hafnian_kernel<false><<<blocks, 32 * wpb, wpb * per_warp, st>>>(a, kmax);
+        }
+        if (e != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = report(PQ_ERR_CUDA, "hafnian kernel failed");
+    } else {
+        cudaStreamSynchronize(st);
+    }
+    cudaFree(desc_d);
+    cudaFree(meta_d);
+    cudaFree(tasks_d);
+    cudaFree(part_d);
+    cudaFree(cnt_d);
+    return rc;
+}
+
+}  // namespace pqi
+
+extern "C" int pq_hafnian_repeated(const pq_c128* mats, const int64_t* mat_off, const int32_t* k,
+                                   const int32_t* rep, const int64_t* rep_off, int64_t batch,
+                                   pq_c128* out, void* stream)
+{
+    return pqi::run_hafnians(mats, mat_off, k, rep, rep_off, nullptr, batch, out, stream);
+}
+
+extern "C" int pq_loop_hafnian_repeated(const pq_c128* mats, const pq_c128* gamma,
+                                        const int64_t* mat_off, const int32_t* k,
+                                        const int32_t* rep, const int64_t* rep_off, int64_t batch,
+                                        pq_c128* out, void* stream)
+{
+    if (batch > 0 && !gamma)
+        return pqi::report(PQ_ERR_ARG, "null gamma");
+    return pqi::run_hafnians(mats, mat_off, k, rep, rep_off, gamma, batch, out, stream);
+}

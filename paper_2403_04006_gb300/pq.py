@@ -74,6 +74,8 @@ _SIGNATURES = {
     "pq_permanent_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp]),
     "pq_bs_sample": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "pq_bs_probs_lossy": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp]),
+    "pq_hafnian_repeated": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "pq_loop_hafnian_repeated": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "pq_last_error": (ctypes.c_char_p, []),
@@ -217,6 +219,27 @@ def pq_bs_sample(U_ptr, m: int, input_occ: np.ndarray, col_order: np.ndarray,
                                        out.ctypes.data if out.size else None, stream),
            "pq_bs_sample")
     return out
+
+
+def pq_hafnian_repeated(mats_ptr, mat_off: np.ndarray, k: np.ndarray, rep: np.ndarray,
+                        rep_off: np.ndarray, out_ptr, stream, gamma_ptr=None, loop: bool = False):
+    """Hafnians (or, with ``loop``, loop hafnians with loop weights at
+    ``gamma_ptr``) of bases repeated by ``rep``; mat_off / k / rep / rep_off
+    are host arrays, mats, gamma and out device pointers."""
+    mo = np.ascontiguousarray(mat_off, dtype=np.int64)
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    r = np.ascontiguousarray(rep, dtype=np.int32)
+    ro = np.ascontiguousarray(rep_off, dtype=np.int64)
+    nb = kk.shape[0]
+    lib = load_library()
+    args = (mo.ctypes.data if nb else None, kk.ctypes.data if nb else None,
+            r.ctypes.data if r.size else (kk.ctypes.data if nb else None),
+            ro.ctypes.data if nb else None, nb, out_ptr, stream)
+    if loop:
+        _check(lib.pq_loop_hafnian_repeated(mats_ptr, gamma_ptr, *args),
+               "pq_loop_hafnian_repeated")
+    else:
+        _check(lib.pq_hafnian_repeated(mats_ptr, *args), "pq_hafnian_repeated")
 
 
 def pq_bs_probs_lossy(V_ptr, eta_ptr, W_ptr, m: int, input_occ: np.ndarray,

@@ -280,3 +280,48 @@ def sampler_draws(nsamples: int, n: int, seed: int):
         if nsamples else np.zeros((0, n), dtype=np.int32)
     uniforms = rng.random((nsamples, n))
     return np.ascontiguousarray(order.reshape(nsamples, n)), np.ascontiguousarray(uniforms)
+
+
+def gbs_matrix(k: int, rng: np.random.Generator, squeezing: float = math.asinh(1.0)):
+    """Symmetric k x k matrix U diag(tanh r) U^T of a Haar interferometer U
+    after k equal single-mode squeezers (the Gaussian boson-sampling setting
+    of Sec. 4.1 / Fig. gaussian_boson_sampling_benchmark, r = arcsinh 1)."""
+    U = haar_unitary(k, rng)
+    A = (U * math.tanh(squeezing)) @ U.T
+    return np.ascontiguousarray((A + A.T) / 2)  # exactly symmetric
+
+
+def paper_repeated_hafnian(k: int, loop: bool = False, seed_stream: int = 0):
+    """Workload of the paper's repeated (loop) hafnian benchmarks (Figs.
+    hafnian and loop_hafnian): a k x k symmetric GBS matrix with every index
+    repeated twice (N = 2k); for the loop hafnian also loop weights gamma with
+    entries ~ CN(0, 1/2).  Returns (B, r, gamma or None)."""
+    rng = rng_for(8, 100 * k + seed_stream + (50 if loop else 0))
+    B = gbs_matrix(k, rng)
+    gamma = None
+    if loop:
+        gamma = (rng.standard_normal(k) + 1j * rng.standard_normal(k)) * 0.5
+    return B, np.full(k, 2, dtype=np.int32), gamma
+
+
+def hafnian_batch(count: int, kmin: int = 1, kmax: int = 8, rmax: int = 3, seed_stream: int = 0):
+    """Ragged batch of repeated-hafnian items: k ~ U{kmin..kmax}, repetitions
+    ~ U{0..rmax} per index, GBS base matrices, loop weights ~ CN(0, 1/2).
+    Returns packed (mats, mat_off, k, rep, rep_off, gamma)."""
+    rng = rng_for(9, seed_stream)
+    mats, gam, reps = [], [], []
+    ks = rng.integers(kmin, kmax + 1, size=count)
+    mat_off = np.zeros(count, dtype=np.int64)
+    rep_off = np.zeros(count, dtype=np.int64)
+    mo = ro = 0
+    for b, k in enumerate(ks):
+        k = int(k)
+        mats.append(gbs_matrix(k, rng).reshape(-1))
+        reps.append(rng.integers(0, rmax + 1, size=k).astype(np.int32))
+        gam.append((rng.standard_normal(k) + 1j * rng.standard_normal(k)) * 0.5)
+        mat_off[b], rep_off[b] = mo, ro
+        mo += k * k
+        ro += k
+    cat = (lambda xs, dt: np.concatenate(xs).astype(dt) if xs else np.zeros(0, dtype=dt))
+    return (cat(mats, np.complex128), mat_off, ks.astype(np.int32), cat(reps, np.int32), rep_off,
+            cat(gam, np.complex128))
