@@ -352,6 +352,16 @@ int pq_plan_item_info(int32_t k, int32_t l, const int32_t* row_mult, const int32
  * its direction (+1 / -1) to host arrays digit[steps], dir[steps]. */
 int pq_gray_walk(const int32_t* radix, int32_t ndig, int64_t steps, int32_t* digit, int32_t* dir);
 
+/* The factors the loop-hafnian kernel evaluates its degree-N polynomial
+ * sum_{j <= N/2} q^j l^{N-2j} / (j! (N-2j)!) with (host only; no GPU needed):
+ * out[0] = 1 / J!, J = floor(N/2); then for each pair of the real roots
+ * z_m = -1/(2 x_m^2) (x_m the positive roots of the Hermite polynomial He_N,
+ * ascending) a = -(z_1 + z_2) and b = z_1 z_2; then, if J is odd, the last
+ * root.  The polynomial is out[0] prod_pairs (q^2 + a q s + b s^2)
+ * [(q - z s)] [l], s = l^2.  out: host, J + 1 doubles.
+ * Errors: PQ_ERR_ARG (N outside [0, PQ_MAX_N], null out). */
+int pq_loop_poly_factors(int32_t N, double* out);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* pq_last_error(void);
 

@@ -19,11 +19,22 @@
 // one copy of the least repeated index keeping a + sign (top = r - 1 there;
 // the summand is even under flipping every sign).  A Gray step changes one
 // x_r by D = -+2:  q += D y_r + 2 B_rr with y = B x, then y_j += D B_jr and
-// l += D gamma_r: O(k) work per term.  q^n is taken by repeated squaring; the
-// loop polynomial by a homogeneous Horner scheme in q and l^2.
+// l += D gamma_r.  Inside a chunk only the J low digits move, so the walk
+// reads y at the J low rows alone and keeps only those (2J DFMA a step
+// instead of 2k); y is formed in full once per chunk for the start value of
+// q.  q^n is taken by repeated squaring.  The loop polynomial is homogeneous
+// of degree N/2 in (q, l^2): sum_j q^j s^{J-j} / (j! (N-2j)!) with s = l^2,
+// J = floor(N/2), equals c_J prod_m (q - z_m s) (times l for odd N), where
+// z_m = -1 / (2 x_m^2) and x_m runs over the positive roots of the Hermite
+// polynomial He_N (substituting z = -1/(2x^2) turns the sum into
+// x^{-N} He_N(x) / N!).  The roots are real, found once per N on the host by
+// Sturm-count bisection on the Jacobi matrix of He_N, and the kernel
+// multiplies the factors in pairs: 2 FP64 operations per unit of N instead
+// of Horner's 5.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -34,7 +45,7 @@
 
 namespace pqi {
 
-constexpr int kHafMaxHalf = PQ_MAX_N / 2;  // Horner coefficients j = 0 .. N/2
+constexpr int kHafMaxHalf = PQ_MAX_N / 2;  // loop-polynomial factors j = 1 .. N/2
 
 // Per (loop) hafnian: k kept base indices, digits as for the permanent.
 struct alignas(16) HafDesc {
@@ -43,6 +54,7 @@ struct alignas(16) HafDesc {
     int32_t meta;          // ridx[k], rmul[k], drow[nd], drad[nd], dtop[nd]
     int32_t ndig, J, ntasks, slot0;
     int32_t weighted, trivial;  // trivial: result = value (0 for odd N, 1 for N = 0)
+    int32_t coef_off;           // loop hafnian: factors of its loop polynomial in loopc
     double value;               // final multiplier (or the trivial result)
 };
 
@@ -53,55 +65,91 @@ struct HafArgs {
     int64_t ntasks;
     const double2* src;
     const double2* gamma;  // loop weights (loop hafnian only)
+    const double* loopc;   // loop-polynomial factors per distinct N (loop hafnian only)
     double2* out;
     double* partials;
     int32_t* counters;
 };
 
-// Shared memory of one warp: M (k x k), y0 = B r (k), gamma (k),
-// y (k x 32, lane-major), Horner coefficients, low-digit rows.
-__host__ __device__ inline int haf_warp_smem_bytes(int kmax)
+// Shared memory of one warp: M (k x k), y0 = B r (k), gamma (k), y (k x 32,
+// lane-major), y at the low rows (J x 32, lane-major), B restricted to the
+// low rows (J x J), Horner coefficients, low-digit rows.
+__host__ __device__ inline int haf_warp_smem_bytes(int kmax, int jmax)
 {
-    int bytes = (kmax * kmax + 2 * kmax + 32 * kmax) * 16 + (kHafMaxHalf + 1) * 8 + 16 * 4;
+    int bytes = (kmax * kmax + 2 * kmax + 32 * kmax + 32 * jmax + jmax * jmax) * 16 +
+                (kHafMaxHalf + 1) * 8 + 16 * 4;
     return (bytes + 15) & ~15;
 }
 
-// p = q^n, n >= 1 (warp-uniform n)
-__device__ __forceinline__ double2 cpow_n(double2 q, int n)
+// q^E by the binary method, unrolled at compile time.
+template <int E>
+__device__ __forceinline__ double2 cpow_c(double2 q)
 {
-    double2 p = q;
-    int top = 31 - __clz(n);
-#pragma unroll 1
-    for (int b = top - 1; b >= 0; --b) {
-        p = cmul(p, p);
-        if ((n >> b) & 1)
-            p = cmul(p, q);
+    if constexpr (E == 1) {
+        return q;
+    } else if constexpr ((E & 1) == 0) {
+        const double2 h = cpow_c<E / 2>(q);
+        return cmul(h, h);
+    } else {
+        return cmul(cpow_c<E - 1>(q), q);
     }
-    return p;
 }
 
-// sum_{j=0}^{N/2} c_j q^j l^{N-2j} by h <- h q + c_j (l^2)^{N/2-j}
-__device__ __forceinline__ double2 loop_poly(double2 q, double2 l, int N, const double* cj)
+// q^n for a warp-uniform 1 <= n <= PQ_MAX_N / 2: one uniform branch to
+// straight-line code (a runtime bit loop would issue its conditional
+// multiplies under false predicates).
+__device__ __forceinline__ double2 cpow_n(double2 q, int n)
 {
-    const int J = N >> 1;
-    const double2 s = cmul(l, l);
-    double2 h = make_double2(cj[J], 0.0);
-    double2 w = make_double2(1.0, 0.0);
-#pragma unroll 1
-    for (int j = J - 1; j >= 0; --j) {
-        w = cmul(w, s);
-        h = cmul(h, q);
-        h.x = __fma_rn(cj[j], w.x, h.x);
-        h.y = __fma_rn(cj[j], w.y, h.y);
+    switch (n) {
+#define PQ_POW_CASE(E) \
+    case E: return cpow_c<E>(q);
+        PQ_POW_CASE(1) PQ_POW_CASE(2) PQ_POW_CASE(3) PQ_POW_CASE(4) PQ_POW_CASE(5)
+        PQ_POW_CASE(6) PQ_POW_CASE(7) PQ_POW_CASE(8) PQ_POW_CASE(9) PQ_POW_CASE(10)
+        PQ_POW_CASE(11) PQ_POW_CASE(12) PQ_POW_CASE(13) PQ_POW_CASE(14) PQ_POW_CASE(15)
+        PQ_POW_CASE(16) PQ_POW_CASE(17) PQ_POW_CASE(18) PQ_POW_CASE(19) PQ_POW_CASE(20)
+        PQ_POW_CASE(21) PQ_POW_CASE(22) PQ_POW_CASE(23) PQ_POW_CASE(24)
+#undef PQ_POW_CASE
+    default: return q;  // not reached: the planner bounds n by PQ_MAX_N / 2
     }
-    if (N & 1)
+}
+static_assert(PQ_MAX_N / 2 == 24, "cpow_n covers exponents up to 24");
+
+// sum_{j=0}^{N/2} q^j l^{N-2j} / (j! (N-2j)!) from the factors cf = [c_J,
+// a_0, b_0, a_1, b_1, ..., (z_last)]: each of the P = floor(N/4) pairs of
+// roots gives q^2 + a q s + b s^2 (a = -(z1 + z2), b = z1 z2); an odd root
+// count J leaves one factor q - z s; odd N one factor l.  JODD and NODD are
+// template flags so that no factor is issued under a false predicate.
+template <bool JODD, bool NODD>
+__device__ __forceinline__ double2 loop_poly(double2 q, double2 l, int P, const double* cf)
+{
+    const double2 s = cmul(l, l);
+    double2 h = make_double2(cf[0], 0.0);
+    if (P) {
+        const double2 q2 = cmul(q, q), qs = cmul(q, s), s2 = cmul(s, s);
+#pragma unroll 1
+        for (int p = 0; p < P; ++p) {
+            const double a = cf[1 + 2 * p], b = cf[2 + 2 * p];
+            double2 t;
+            t.x = __fma_rn(b, s2.x, __fma_rn(a, qs.x, q2.x));
+            t.y = __fma_rn(b, s2.y, __fma_rn(a, qs.y, q2.y));
+            h = cmul(h, t);
+        }
+    }
+    if (JODD) {
+        const double z = cf[1 + 2 * P];
+        double2 t;
+        t.x = __fma_rn(-z, s.x, q.x);
+        t.y = __fma_rn(-z, s.y, q.y);
+        h = cmul(h, t);
+    }
+    if (NODD)
         h = cmul(h, l);
     return h;
 }
 
 template <bool LOOP>
-__device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, int kmax, int& staged,
-                         int lane)
+__device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, int kmax, int jmax,
+                         int& staged, int lane)
 {
     const HafDesc D = a.desc[t.perm];
     const int k = D.k, J = D.J, nd = D.ndig;
@@ -109,7 +157,9 @@ __device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, in
     double2* y0 = M + kmax * kmax;
     double2* gam = y0 + kmax;
     double2* Y = gam + kmax;
-    double* cj = reinterpret_cast<double*>(Y + 32 * kmax);
+    double2* YL = Y + 32 * kmax;
+    double2* Bll = YL + 32 * jmax;
+    double* cj = reinterpret_cast<double*>(Bll + jmax * jmax);
     int32_t* lowrow = reinterpret_cast<int32_t*>(cj + kHafMaxHalf + 1);
     const int32_t* ridx = a.meta + D.meta;
     const int32_t* rmul = ridx + k;
@@ -130,16 +180,14 @@ __device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, in
             if (LOOP) {
                 for (int i = lane; i < k; i += kWarp)
                     gam[i] = a.gamma[D.gam_off + ridx[i]];
-                for (int j = lane; j <= D.N / 2; j += kWarp) {  // 1 / (j! (N-2j)!)
-                    double f = 1.0;
-                    for (int i = 2; i <= j; ++i)
-                        f *= (double)i;
-                    for (int i = 2; i <= D.N - 2 * j; ++i)
-                        f *= (double)i;
-                    cj[j] = 1.0 / f;
-                }
+                for (int j = lane; j <= D.N / 2; j += kWarp)
+                    cj[j] = a.loopc[D.coef_off + j];
             }
             __syncwarp();
+            for (int e = lane; e < J * J; e += kWarp) {  // B at the low rows
+                const int u = e / J, v = e - u * J;
+                Bll[e] = M[lowrow[u] * k + lowrow[v]];
+            }
             for (int j = lane; j < k; j += kWarp) {  // y0 = B r
                 double2 s = make_double2(0.0, 0.0);
                 for (int i = 0; i < k; ++i) {
@@ -218,6 +266,10 @@ __device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, in
         }
         q.x *= 0.5;
         q.y *= 0.5;
+        double2* yl = YL + lane;
+#pragma unroll 1
+        for (int e = 0; e < J; ++e)
+            yl[e * 32] = y[lowrow[e] * 32];
         double whigh = active ? (double)whigh_u : 0.0;
         if (gpar & 1)
             whigh = -whigh;
@@ -234,49 +286,86 @@ __device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, in
         }
         const bool weighted = D.weighted != 0;
         const int n = D.n, N = D.N;
+        const int form = ((N >> 1) & 1) * 2 + (N & 1), P = N >> 2;
         double wlow = 1.0;
         double2 acc = make_double2(0.0, 0.0);
         double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
         const int64_t L = D.L;
-        int blk = 0;
-#pragma unroll 1
-        for (int64_t s = 0; s < L; ++s) {
-            const double2 p = LOOP ? loop_poly(q, l, N, cj) : cpow_n(q, n);
-            const double ws = (s & 1) ? -wlow : wlow;
-            acc.x = __fma_rn(ws, p.x, acc.x);
-            acc.y = __fma_rn(ws, p.y, acc.y);
-            if (s + 1 < L) {
-                int up;
-                const int d = low_step(wk, up);
-                const int row = lowrow[d];
-                const double delta = up > 0 ? -2.0 : 2.0;
-                const double2 yr = y[row * 32];
-                const double2 brr = M[row * k + row];
-                q.x = __fma_rn(delta, yr.x, q.x);
-                q.y = __fma_rn(delta, yr.y, q.y);
-                q.x = __fma_rn(2.0, brr.x, q.x);
-                q.y = __fma_rn(2.0, brr.y, q.y);
-                if (LOOP) {
-                    l.x = __fma_rn(delta, gam[row].x, l.x);
-                    l.y = __fma_rn(delta, gam[row].y, l.y);
+        // The term's polynomial value; the uniform switches pick straight-line
+        // code for the exponent or the loop-polynomial shape, so no FP64
+        // instruction is issued under a false predicate.
+        auto value = [&]() -> double2 {
+            if (LOOP) {
+                switch (form) {
+                case 0: return loop_poly<false, false>(q, l, P, cj);
+                case 1: return loop_poly<false, true>(q, l, P, cj);
+                case 2: return loop_poly<true, false>(q, l, P, cj);
+                default: return loop_poly<true, true>(q, l, P, cj);
                 }
+            }
+            return cpow_n(q, n);
+        };
+        auto term_pos = [&]() {
+            const double2 p = value();
+            acc.x = __fma_rn(wlow, p.x, acc.x);
+            acc.y = __fma_rn(wlow, p.y, acc.y);
+        };
+        auto term_neg = [&]() {
+            const double2 p = value();
+            acc.x = __fma_rn(-wlow, p.x, acc.x);
+            acc.y = __fma_rn(-wlow, p.y, acc.y);
+        };
+        // One Gray step: x_row moves by -+2.
+        auto step = [&]() {
+            int up;
+            const int d = low_step(wk, up);
+            const double delta = up > 0 ? -2.0 : 2.0;
+            const double2 yr = yl[d * 32];
+            const double2* Bd = Bll + d * J;
+            const double2 brr = Bd[d];
+            q.x = __fma_rn(delta, yr.x, q.x);
+            q.y = __fma_rn(delta, yr.y, q.y);
+            q.x = __fma_rn(2.0, brr.x, q.x);
+            q.y = __fma_rn(2.0, brr.y, q.y);
+            if (LOOP) {
+                const double2 gr = gam[lowrow[d]];
+                l.x = __fma_rn(delta, gr.x, l.x);
+                l.y = __fma_rn(delta, gr.y, l.y);
+            }
 #pragma unroll 1
-                for (int j = 0; j < k; ++j) {
-                    const double2 b = M[j * k + row];
-                    double2 v = y[j * 32];
-                    v.x = __fma_rn(delta, b.x, v.x);
-                    v.y = __fma_rn(delta, b.y, v.y);
-                    y[j * 32] = v;
-                }
-                if (weighted && ((wk.radm1 >> (4 * d)) & 15u) > 1u)
-                    wlow = (double)low_weight(wk, J);
+            for (int e = 0; e < J; ++e) {
+                const double2 b = Bd[e];
+                double2 v = yl[e * 32];
+                v.x = __fma_rn(delta, b.x, v.x);
+                v.y = __fma_rn(delta, b.y, v.y);
+                yl[e * 32] = v;
             }
-            if (++blk == 16) {
-                blk = 0;
-                dd_acc(rh, rl, acc.x);
-                dd_acc(ih, il, acc.y);
-                acc = make_double2(0.0, 0.0);
+            if (weighted && ((wk.radm1 >> (4 * d)) & 15u) > 1u)
+                wlow = (double)low_weight(wk, J);
+        };
+        // Term 0 has sign +; then pairs (odd: -, even: +), folded into the
+        // double-double sums every 16 terms by the outer loop.
+        term_pos();
+        int64_t s = 1;
+#pragma unroll 1
+        while (s < L) {
+            const int npairs = (int)min((L - s) >> 1, (int64_t)8);
+#pragma unroll 1
+            for (int i = 0; i < npairs; ++i) {
+                step();
+                term_neg();
+                step();
+                term_pos();
             }
+            s += 2 * npairs;
+            if (npairs == 0) {  // one (odd) term left
+                step();
+                term_neg();
+                s += 1;
+            }
+            dd_acc(rh, rl, acc.x);
+            dd_acc(ih, il, acc.y);
+            acc = make_double2(0.0, 0.0);
         }
         dd_acc(rh, rl, acc.x);
         dd_acc(ih, il, acc.y);
@@ -338,11 +427,11 @@ __device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, in
 
 // Persistent: every warp takes tasks from a global queue (counters[0]).
 template <bool LOOP>
-__global__ void __launch_bounds__(256) hafnian_kernel(HafArgs a, int kmax)
+__global__ void __launch_bounds__(256, 1) hafnian_kernel(HafArgs a, int kmax, int jmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* raw = smem_raw + warp * haf_warp_smem_bytes(kmax);
+    unsigned char* raw = smem_raw + warp * haf_warp_smem_bytes(kmax, jmax);
     int staged = -1;
     for (;;) {
         int q = 0;
@@ -351,8 +440,80 @@ __global__ void __launch_bounds__(256) hafnian_kernel(HafArgs a, int kmax)
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= a.ntasks)
             break;
-        haf_task<LOOP>(a, a.tasks[q], raw, kmax, staged, lane);
+        haf_task<LOOP>(a, a.tasks[q], raw, kmax, jmax, staged, lane);
     }
+}
+
+// Positive roots of the Hermite polynomial He_N (He_{k+1} = x He_k - k He_{k-1}),
+// ascending: bisection on the number of eigenvalues of its Jacobi matrix
+// (zero diagonal, off-diagonal sqrt(k)) below t, counted by the signs of the
+// LDL^T pivots of J - t, then Newton steps on He_N.
+static std::vector<double> hermite_positive_roots(int N)
+{
+    auto count_below = [N](double t) {
+        int c = 0;
+        double d = -t;
+        c += d < 0.0;
+        for (int k = 1; k < N; ++k) {
+            if (d == 0.0)
+                d = 1e-300;
+            d = -t - (double)k / d;
+            c += d < 0.0;
+        }
+        return c;
+    };
+    const int J = N / 2;
+    const double top = 2.0 * std::sqrt((double)N) + 2.0;  // every root lies below
+    std::vector<double> x;
+    for (int i = N - J + 1; i <= N; ++i) {  // i-th smallest root
+        double lo = 0.0, hi = top;
+        for (int it = 0; it < 2000; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi)
+                break;
+            if (count_below(mid) >= i)
+                hi = mid;
+            else
+                lo = mid;
+        }
+        double r = 0.5 * (lo + hi);
+        for (int it = 0; it < 2; ++it) {
+            double p0 = 1.0, p1 = r;  // He_{k-1}, He_k
+            for (int k = 1; k < N; ++k) {
+                const double p2 = r * p1 - (double)k * p0;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (p0 != 0.0)
+                r -= p1 / ((double)N * p0);
+        }
+        x.push_back(r);
+    }
+    return x;
+}
+
+// Factors of the loop polynomial of size N for loop_poly: [c_J, a_0, b_0,
+// ..., (z_last)], J + 1 numbers.
+static std::vector<double> loop_factors(int N)
+{
+    const int J = N / 2;
+    std::vector<double> cf;
+    double cJ = 1.0;
+    for (int i = 2; i <= J; ++i)
+        cJ /= (double)i;  // 1 / (J! (N - 2J)!), N - 2J <= 1
+    cf.push_back(cJ);
+    const std::vector<double> x = hermite_positive_roots(N);
+    std::vector<double> z;
+    for (double v : x)
+        z.push_back(-1.0 / (2.0 * v * v));
+    int m = 0;
+    for (; m + 1 < J; m += 2) {
+        cf.push_back(-(z[m] + z[m + 1]));
+        cf.push_back(z[m] * z[m + 1]);
+    }
+    if (m < J)
+        cf.push_back(z[m]);
+    return cf;
 }
 
 static double factorial_h(int n)
@@ -373,19 +534,29 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
         return report(PQ_ERR_ARG, "null argument or negative batch");
     if (batch > (int64_t(1) << 30))
         return report(PQ_ERR_UNSUPPORTED, "batch above 2^30");
+    int dev = 0, sms = 1;
+    if (batch > 0 && (cudaGetDevice(&dev) != cudaSuccess ||
+                      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                          cudaSuccess))
+        return report(PQ_ERR_CUDA, "no CUDA device");
+    struct Dg {
+        int rad, row, top;
+    };
+    struct Item {
+        std::vector<int32_t> ridx, rm;
+        std::vector<Dg> dg;
+    };
     std::vector<HafDesc> desc(batch);
-    std::vector<int32_t> meta;
-    std::vector<Task> tasks;
-    std::vector<double> cost;
-    int kmax = 1;
-    int32_t slot = 0;
+    std::vector<Item> items(batch);
+    double t_total = 0.0;
+    // Pass 1: kept indices, digits and term counts.
     for (int64_t b = 0; b < batch; ++b) {
         HafDesc& D = desc[b];
+        Item& it = items[b];
         std::memset(&D, 0, sizeof(D));
         if (k[b] < 0 || k[b] > PQ_MAX_DIM || mat_off[b] < 0 || rep_off[b] < 0)
             return report(PQ_ERR_ARG, "bad size or offset");
         const int32_t* r = rep + rep_off[b];
-        std::vector<int32_t> ridx, rm;
         int N = 0;
         for (int i = 0; i < k[b]; ++i) {
             if (r[i] < 0)
@@ -393,8 +564,8 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
             if (r[i] > PQ_MAX_N)
                 return report(PQ_ERR_UNSUPPORTED, "expanded size above PQ_MAX_N");
             if (r[i] > 0) {
-                ridx.push_back(i);
-                rm.push_back(r[i]);
+                it.ridx.push_back(i);
+                it.rm.push_back(r[i]);
                 N += r[i];
             }
         }
@@ -405,70 +576,113 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
         D.ld = k[b];
         D.N = N;
         D.n = N / 2;
-        D.slot0 = slot;
         if (N == 0 || (!loop && (N & 1))) {
             D.trivial = 1;
             D.value = (N == 0) ? 1.0 : 0.0;
+            continue;
+        }
+        const int kk = (int)it.ridx.size();
+        D.k = kk;
+        D.value = loop ? 1.0 : 1.0 / factorial_h(N / 2);
+        // Digits: one copy of the least repeated index fixed (radix r_f), the
+        // others radix r_i + 1; ascending radix so that small ones walk inside
+        // a chunk.
+        const int f = (int)(std::min_element(it.rm.begin(), it.rm.end()) - it.rm.begin());
+        int64_t T = 1;
+        for (int i = 0; i < kk; ++i) {
+            const int rad = (i == f) ? it.rm[i] : it.rm[i] + 1;
+            if (rad < 2)
+                continue;
+            it.dg.push_back({rad, i, (i == f) ? it.rm[i] - 1 : it.rm[i]});
+            if (T > (int64_t(1) << 62) / rad)
+                return report(PQ_ERR_UNSUPPORTED, "term count above 2^62");
+            T *= rad;
+        }
+        std::stable_sort(it.dg.begin(), it.dg.end(),
+                         [](const Dg& x, const Dg& y) { return x.rad < y.rad; });
+        D.T = T;
+        D.ndig = (int)it.dg.size();
+        t_total += (double)T;
+    }
+    // Pass 2: chunks and tasks.  Every item gets a share of about 64 warp
+    // tasks per SM in proportion to its terms, so that one large hafnian still
+    // fills the GPU.
+    const double want_tasks = 64.0 * sms;
+    std::vector<int32_t> meta;
+    std::vector<Task> tasks;
+    std::vector<double> cost;
+    std::vector<double> loopc;
+    std::vector<int32_t> coef_at(PQ_MAX_N + 1, -1);
+    int kmax = 1, jmax = 1;
+    int32_t slot = 0;
+    for (int64_t b = 0; b < batch; ++b) {
+        HafDesc& D = desc[b];
+        Item& it = items[b];
+        D.slot0 = slot;
+        if (D.trivial) {
             D.ntasks = 1;
             tasks.push_back(Task{(int32_t)b, 0});
             cost.push_back(0.0);
             slot += 1;
             continue;
         }
-        const int kk = (int)ridx.size();
+        const int kk = D.k, N = D.N;
+        const int64_t T = D.T;
         kmax = std::max(kmax, kk);
-        D.k = kk;
-        D.value = loop ? 1.0 : 1.0 / factorial_h(N / 2);
-        // Digits: one copy of the least repeated index fixed (radix r_f), the
-        // others radix r_i + 1; ascending radix so that small ones walk inside
-        // a chunk.
-        const int f = (int)(std::min_element(rm.begin(), rm.end()) - rm.begin());
-        struct Dg {
-            int rad, row, top;
-        };
-        std::vector<Dg> dg;
-        int64_t T = 1;
-        for (int i = 0; i < kk; ++i) {
-            const int rad = (i == f) ? rm[i] : rm[i] + 1;
-            if (rad < 2)
-                continue;
-            dg.push_back({rad, i, (i == f) ? rm[i] - 1 : rm[i]});
-            if (T > (int64_t(1) << 62) / rad)
-                return report(PQ_ERR_UNSUPPORTED, "term count above 2^62");
-            T *= rad;
+        if (loop) {
+            if (coef_at[N] < 0) {
+                coef_at[N] = (int32_t)loopc.size();
+                const std::vector<double> cf = loop_factors(N);
+                loopc.insert(loopc.end(), cf.begin(), cf.end());
+            }
+            D.coef_off = coef_at[N];
         }
-        std::stable_sort(dg.begin(), dg.end(), [](const Dg& x, const Dg& y) { return x.rad < y.rad; });
-        D.T = T;
-        D.ndig = (int)dg.size();
-        // Chunk length: at most 1024 terms and at least 32 chunks when T allows.
-        const int64_t target = std::max<int64_t>(1, std::min<int64_t>(T / kWarp, 1024));
+        // Chunk length L = product of the J low radices, at most 4096 terms,
+        // at most T / (32 x the item's task share), and J minimising the FP64
+        // work per term: 2J + 8 for the walk plus 2k(ndig - J) + 4k + 64 per
+        // chunk for the start value.
+        const double share = std::max(1.0, std::ceil(want_tasks * (double)T / t_total));
+        const int64_t cap = std::max<int64_t>(
+            1, std::min<int64_t>(4096, (int64_t)((double)T / (kWarp * share))));
         int J = 0;
         int64_t L = 1;
-        while (J < D.ndig && J < kMaxLowDigits && dg[J].rad <= kMaxLowRadix &&
-               L * dg[J].rad <= target) {
-            L *= dg[J].rad;
-            ++J;
+        {
+            double best = 1e300;
+            int64_t Lc = 1;
+            for (int j = 0;; ++j) {
+                const double c = 2.0 * j + 8.0 + (2.0 * kk * (D.ndig - j) + 4.0 * kk + 64.0) / Lc;
+                if (c < best) {
+                    best = c;
+                    J = j;
+                    L = Lc;
+                }
+                if (j >= D.ndig || j >= kMaxLowDigits || it.dg[j].rad > kMaxLowRadix ||
+                    Lc * it.dg[j].rad > cap)
+                    break;
+                Lc *= it.dg[j].rad;
+            }
         }
+        jmax = std::max(jmax, J);
         D.J = J;
         D.L = L;
         D.nchunks = T / L;
         for (int d = 0; d < J; ++d)
-            if (dg[d].rad > 2)
+            if (it.dg[d].rad > 2)
                 D.weighted = 1;
         const int64_t nt = (D.nchunks + kWarp - 1) / kWarp;
         if (nt + slot > (int64_t(1) << 30))
             return report(PQ_ERR_UNSUPPORTED, "too many tasks");
         D.ntasks = (int32_t)nt;
         D.meta = (int32_t)meta.size();
-        meta.insert(meta.end(), ridx.begin(), ridx.end());
-        meta.insert(meta.end(), rm.begin(), rm.end());
-        for (const Dg& d : dg)
+        meta.insert(meta.end(), it.ridx.begin(), it.ridx.end());
+        meta.insert(meta.end(), it.rm.begin(), it.rm.end());
+        for (const Dg& d : it.dg)
             meta.push_back(d.row);
-        for (const Dg& d : dg)
+        for (const Dg& d : it.dg)
             meta.push_back(d.rad);
-        for (const Dg& d : dg)
+        for (const Dg& d : it.dg)
             meta.push_back(d.top);
-        const double per_term = loop ? (2.0 * kk + 10.0 * (N / 2) + 12.0) : (2.0 * kk + 24.0);
+        const double per_term = loop ? (2.0 * J + 10.0 * (N / 2) + 12.0) : (2.0 * J + 24.0);
         for (int64_t q = 0; q < nt; ++q) {
             tasks.push_back(Task{(int32_t)b, (int32_t)q});
             cost.push_back((double)L * per_term);
@@ -491,8 +705,10 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
     Task* tasks_d = nullptr;
     double* part_d = nullptr;
     int32_t* cnt_d = nullptr;
+    double* loopc_d = nullptr;
     int rc = PQ_OK;
-    if (cudaMalloc((void**)&desc_d, sizeof(HafDesc) * batch) != cudaSuccess ||
+    if (cudaMalloc((void**)&loopc_d, sizeof(double) * std::max<size_t>(loopc.size(), 1)) != cudaSuccess ||
+        cudaMalloc((void**)&desc_d, sizeof(HafDesc) * batch) != cudaSuccess ||
         cudaMalloc((void**)&meta_d, sizeof(int32_t) * std::max<size_t>(meta.size(), 1)) != cudaSuccess ||
         cudaMalloc((void**)&tasks_d, sizeof(Task) * sorted.size()) != cudaSuccess ||
         cudaMalloc((void**)&part_d, sizeof(double) * 4 * std::max<int32_t>(slot, 1)) != cudaSuccess ||
@@ -505,13 +721,12 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
                                            cudaMemcpyHostToDevice, st) != cudaSuccess) ||
          cudaMemcpyAsync(tasks_d, sorted.data(), sizeof(Task) * sorted.size(),
                          cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         (!loopc.empty() && cudaMemcpyAsync(loopc_d, loopc.data(), sizeof(double) * loopc.size(),
+                                            cudaMemcpyHostToDevice, st) != cudaSuccess) ||
          cudaMemsetAsync(cnt_d, 0, sizeof(int32_t) * (batch + 1), st) != cudaSuccess))
         rc = report(PQ_ERR_CUDA, "hafnian upload failed");
     if (rc == PQ_OK) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int per_warp = haf_warp_smem_bytes(kmax);
+        const int per_warp = haf_warp_smem_bytes(kmax, jmax);
         int wpb = 8;
         while (wpb > 1 && wpb * per_warp > 227 * 1024)
             --wpb;
@@ -523,6 +738,7 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
         a.ntasks = (int64_t)sorted.size();
         a.src = reinterpret_cast<const double2*>(mats);
         a.gamma = reinterpret_cast<const double2*>(gamma);
+        a.loopc = loopc_d;
         a.out = reinterpret_cast<double2*>(out);
         a.partials = part_d;
         a.counters = cnt_d;
@@ -533,12 +749,12 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
             e = cudaFuncSetAttribute(hafnian_kernel<true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * per_warp);
             if (e == cudaSuccess)
-                hafnian_kernel<true><<<blocks, 32 * wpb, wpb * per_warp, st>>>(a, kmax);
+                hafnian_kernel<true><<<blocks, 32 * wpb, wpb * per_warp, st>>>(a, kmax, jmax);
         } else {
             e = cudaFuncSetAttribute(hafnian_kernel<false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * per_warp);
             if (e == cudaSuccess)
-                hafnian_kernel<false><<<blocks, 32 * wpb, wpb * per_warp, st>>>(a, kmax);
+                hafnian_kernel<false><<<blocks, 32 * wpb, wpb * per_warp, st>>>(a, kmax, jmax);
         }
         if (e != cudaSuccess || cudaGetLastError() != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
@@ -551,6 +767,7 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
     cudaFree(tasks_d);
     cudaFree(part_d);
     cudaFree(cnt_d);
+    cudaFree(loopc_d);
     return rc;
 }
 
@@ -571,4 +788,14 @@ extern "C" int pq_loop_hafnian_repeated(const pq_c128* mats, const pq_c128* gamm
     if (batch > 0 && !gamma)
         return pqi::report(PQ_ERR_ARG, "null gamma");
     return pqi::run_hafnians(mats, mat_off, k, rep, rep_off, gamma, batch, out, stream);
+}
+
+extern "C" int pq_loop_poly_factors(int32_t N, double* out)
+{
+    if (N < 0 || N > PQ_MAX_N || !out)
+        return pqi::report(PQ_ERR_ARG, "N outside [0, PQ_MAX_N] or null output");
+    const std::vector<double> cf = pqi::loop_factors(N);
+    for (size_t i = 0; i < cf.size(); ++i)
+        out[i] = cf[i];
+    return PQ_OK;
 }

@@ -122,6 +122,33 @@ __host__ __device__ __forceinline__ uint64_t binom_u64(int top, int g)
     return r;
 }
 
+// C(top, g) for top, g < 16 (the low digits), Pascal's triangle built at
+// compile time.  On the device the walk reads it from constant memory with a
+// warp-uniform index instead of dividing 64-bit integers at every step.
+struct BinomTable16 {
+    uint16_t v[16][16];
+};
+constexpr BinomTable16 make_binom16()
+{
+    BinomTable16 t{};
+    for (int n = 0; n < 16; ++n) {
+        t.v[n][0] = 1;
+        for (int g = 1; g <= n; ++g)
+            t.v[n][g] = (uint16_t)(t.v[n - 1][g - 1] + (g < n ? t.v[n - 1][g] : 0));
+    }
+    return t;
+}
+static __constant__ BinomTable16 c_binom16 = make_binom16();
+
+__host__ __device__ __forceinline__ uint64_t binom_small(int top, int g)
+{
+#ifdef __CUDA_ARCH__
+    return c_binom16.v[top][g];
+#else
+    return binom_u64(top, g);
+#endif
+}
+
 // C(top, g) in double (exact while it stays below 2^53).
 __device__ __forceinline__ double binom_f64(int top, int g)
 {
@@ -194,7 +221,7 @@ __host__ __device__ __forceinline__ uint64_t low_weight(const LowWalk& w, int J)
         int g = int((w.g >> (4 * d)) & 15u);
         int top = int((w.topp >> (4 * d)) & 15u);
         if (g)
-            r *= binom_u64(top, g);
+            r *= binom_small(top, g);
     }
     return r;
 }

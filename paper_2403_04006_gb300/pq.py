@@ -78,6 +78,7 @@ _SIGNATURES = {
     "pq_loop_hafnian_repeated": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
+    "pq_loop_poly_factors": (_i32, [_i32, _vp]),
     "pq_last_error": (ctypes.c_char_p, []),
     "pq_version": (ctypes.c_char_p, []),
 }
@@ -240,6 +241,13 @@ def pq_hafnian_repeated(mats_ptr, mat_off: np.ndarray, k: np.ndarray, rep: np.nd
                "pq_loop_hafnian_repeated")
     else:
         _check(lib.pq_hafnian_repeated(mats_ptr, *args), "pq_hafnian_repeated")
+
+
+def pq_loop_poly_factors(N: int) -> np.ndarray:
+    """Host-only: the factors of the loop-hafnian polynomial of size N."""
+    out = np.zeros(N // 2 + 1)
+    _check(load_library().pq_loop_poly_factors(N, out.ctypes.data), "pq_loop_poly_factors")
+    return out
 
 
 def pq_bs_probs_lossy(V_ptr, eta_ptr, W_ptr, m: int, input_occ: np.ndarray,

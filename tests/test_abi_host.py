@@ -143,3 +143,38 @@ def test_gray_walk_rejects_too_many_steps(lib):
     assert lib.pq_gray_walk(rad.ctypes.data_as(ctypes.c_void_p), 2, 6,
                             buf.ctypes.data_as(ctypes.c_void_p),
                             buf.ctypes.data_as(ctypes.c_void_p)) == pq.PQ_ERR_ARG
+
+
+def test_loop_poly_factors_closed_forms(lib):
+    # N = 2: He_2 = x^2 - 1, one root z = -1/2;  N = 4: He_4 = x^4 - 6x^2 + 3
+    # gives the pair a = 1, b = 1/12 (q^2/2 + q l^2/2 + l^4/24 = (q^2 + q s + s^2/12)/2)
+    assert np.allclose(pq.pq_loop_poly_factors(2), [1.0, -0.5], rtol=1e-15, atol=0)
+    assert np.allclose(pq.pq_loop_poly_factors(3), [1.0, -1.0 / 6.0], rtol=1e-15, atol=0)
+    assert np.allclose(pq.pq_loop_poly_factors(4), [0.5, 1.0, 1.0 / 12.0], rtol=1e-14, atol=0)
+    assert np.array_equal(pq.pq_loop_poly_factors(0), [1.0])
+    assert np.array_equal(pq.pq_loop_poly_factors(1), [1.0])
+    with pytest.raises(pq.PQError):
+        pq.pq_loop_poly_factors(49)
+
+
+@pytest.mark.parametrize("N", list(range(0, 49)))
+def test_loop_poly_factors_reproduce_the_polynomial(lib, N):
+    """The factored form equals sum_j q^j l^{N-2j} / (j! (N-2j)!) (the degree-N
+    part of exp(q + l) used by the loop hafnian) at random points."""
+    cf = pq.pq_loop_poly_factors(N)
+    J, P = N // 2, N // 4
+    rng = np.random.default_rng(N)
+    for _ in range(4):
+        q, l = complex(*rng.standard_normal(2)), complex(*rng.standard_normal(2))
+        s = l * l
+        terms = [q ** j * l ** (N - 2 * j) / (math.factorial(j) * math.factorial(N - 2 * j))
+                 for j in range(J + 1)]
+        direct, scale = sum(terms), sum(abs(t) for t in terms)
+        h = cf[0]
+        for p in range(P):
+            h *= q * q + cf[1 + 2 * p] * q * s + cf[2 + 2 * p] * s * s
+        if J % 2:
+            h *= q - cf[1 + 2 * P] * s
+        if N % 2:
+            h *= l
+        assert abs(h - direct) <= 1e-13 * scale, (N, h, direct)
