@@ -248,7 +248,7 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
                 w = w || it.drad[d] > 2;
             const double products = (cmax == 1) ? (it.l - 2) : (it.l + cmax - 3);
             const double ppt = 2.0 * it.l + 4.0 * std::max(products, 0.0) + 4.0 + (w ? 2.0 : 0.0);
-            const double ovh = (nd - j) * (2.0 * it.l + 2.0) + 150.0 + 2.0 * it.k;
+            const double ovh = (nd - j) * (2.0 * it.l + 2.0) + 120.0 + 2.0 * it.k;
             const int64_t tasks = (it.T / lj + kWarp - 1) / kWarp;
             return tasks * ((double)lj * ppt + ovh);
         };

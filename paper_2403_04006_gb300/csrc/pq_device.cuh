@@ -75,13 +75,31 @@ __device__ __forceinline__ dd2 shfl_down_dd2(const dd2& v, int off)
 }
 
 // Tree sum over the 32 lanes in a fixed order; lane 0 holds the result.
+// Each level adds the high parts with TwoSum and gathers the exact error and
+// both low parts into the low part (8 FP64 operations per component instead
+// of a renormalised double-double addition's 20); one TwoSum at the end
+// renormalises.  The low part collects at most a few roundings of numbers
+// 2^-53 smaller than the high part, so the sum keeps double-double accuracy.
 __device__ __forceinline__ dd2 warp_sum_dd2(dd2 v)
 {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        dd2 o = shfl_down_dd2(v, off);
-        dd2_add(v, o);
+        const dd2 o = shfl_down_dd2(v, off);
+        double s, e;
+        two_sum(v.rh, o.rh, s, e);
+        v.rh = s;
+        v.rl = __dadd_rn(__dadd_rn(v.rl, o.rl), e);
+        two_sum(v.ih, o.ih, s, e);
+        v.ih = s;
+        v.il = __dadd_rn(__dadd_rn(v.il, o.il), e);
     }
+    double s, e;
+    two_sum(v.rh, v.rl, s, e);
+    v.rh = s;
+    v.rl = e;
+    two_sum(v.ih, v.il, s, e);
+    v.ih = s;
+    v.il = e;
     return v;
 }
 
