@@ -13,8 +13,9 @@ boson-sampling workload and the Clements-mesh forward+backward workload are
 reported in the same JSON line under "extra".
 
 ``--impl reference`` times the CPU oracle (Ryser's formula in FP64 with
-double-double accumulation, all host cores) on a bounded sample of the same
-batch and prints the same line with "impl": "reference".
+double-double accumulation, all host cores) on the same batch (by default the
+whole of it, a few seconds per step on 16 host cores) and prints the same line
+with "impl": "reference".
 
 Under torchrun (N > 1) every rank runs the whole batch on its own GPU (weak
 scaling, no collective on the data path); rank 0 prints the line with the
@@ -339,17 +340,23 @@ def bench_ours(args):
 
     extra = {}
     if rank == 0 and not args.quick:
-        extra = extra_measurements(args, dev, stream, flush)
+        extra = extra_measurements(args, dev, stream, flush, peak_tflops)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = host_cores()
         idx = oracle_sample(pb, args.cpu_sample_terms)
-        secs = run_oracle_sample(pb, idx, threads)
-        cpu = {"value": glynn_terms(pb, idx) / secs, "unit": UNIT, "cores": threads,
+        # repeat the sample until about 10 s of host time have been measured
+        runs, secs = 0, 0.0
+        while runs < 8 and (runs == 0 or secs < 10.0):
+            secs += run_oracle_sample(pb, idx, threads)
+            runs += 1
+        per = secs / runs
+        cpu = {"value": glynn_terms(pb, idx) / per, "unit": UNIT, "cores": threads,
                "kind": "oracle",
-               "sample": f"{len(idx)} of {pb.batch} permanents (stride-7 order), {secs:.1f} s, "
-                         f"Ryser FP64 + double-double accumulation, {cpu_model()}"}
+               "sample": f"{len(idx)} of {pb.batch} permanents (stride-7 order), {runs} run(s), "
+                         f"{per:.2f} s each, Ryser FP64 + double-double accumulation, "
+                         f"{cpu_model()}"}
 
     traffic = profiled_traffic()
     line = {
@@ -385,7 +392,7 @@ def bench_ours(args):
         print(json.dumps(line), flush=True)
 
 
-def extra_measurements(args, dev, stream, flush):
+def extra_measurements(args, dev, stream, flush, peak_tflops):
     """Secondary numbers of the same path, one JSON object each."""
     import torch
 
@@ -422,7 +429,16 @@ def extra_measurements(args, dev, stream, flush):
     stb = plan_b.stats()
     ms = timed(lambda: api.permanent_backward(db, gout, plan_b, stream=stream), 3)
     res["ragged_backward_batched"] = {"terms_per_s": stb["terms"] / ms * 1e3, "ms": ms,
-                                      "tflops": stb["flops_backward"] / ms / 1e9}
+                                      "tflops": stb["flops_backward"] / ms / 1e9,
+                                      "frac": stb["flops_backward"] / ms / 1e9 / peak_tflops}
+    plan_pb = api.Plan.for_batch(pb, method="plain")
+    stp = plan_pb.stats()
+    ms = timed(lambda: api.permanent_backward(db, gout, plan_pb, stream=stream), 1)
+    res["ragged_backward_plain"] = {"terms_per_s": stp["terms"] / ms * 1e3, "ms": ms,
+                                    "tflops": stp["flops_backward"] / ms / 1e9,
+                                    "frac": stp["flops_backward"] / ms / 1e9 / peak_tflops,
+                                    "launches": stp["launches_backward"]}
+    del plan_pb
     del db, plan_p, plan_b
     # single n = 30
     A = W.single_large(30)
@@ -433,7 +449,8 @@ def extra_measurements(args, dev, stream, flush):
     st = plan30.stats()
     ms = timed(lambda: api.permanent_batched(db30, plan30, out=out30, stream=stream), 3)
     res["single_n30"] = {"terms_per_s": st["terms"] / ms * 1e3, "ms": ms,
-                         "tflops": st["flops_forward"] / ms / 1e9}
+                         "tflops": st["flops_forward"] / ms / 1e9,
+                         "frac": st["flops_forward"] / ms / 1e9 / peak_tflops}
     # the paper's repeated-permanent benchmark shape (Sec. 4.2, Fig. permanent):
     # k x k Haar block, every row and column repeated twice, one launch each
     sweep = {}
@@ -538,8 +555,9 @@ def main(argv=None):
     ap.add_argument("--workload", choices=["ragged", "ragged4096", "single30"], default="ragged",
                     help="ragged is the benchmark; the others are profiling cases")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-terms", type=float, default=1.5e8,
-                    help="Ryser terms of the oracle sample (about 10-30 s on the host)")
+    ap.add_argument("--cpu-sample-terms", type=float, default=math.inf,
+                    help="Ryser terms of the oracle sample (default: the whole batch, "
+                         "about 2-3 s on 16 host cores; repeated to about 10 s)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
