@@ -275,7 +275,14 @@ int pq_autotune(pq_plan* plan, const pq_batch* b, const pq_c128* U, void* stream
  * non-unit weight), FP64 instructions the forward kernel needs for its terms
  * (Gray step, products, fused accumulation, weights, double-double fold;
  * each DADD, DMUL or DFMA counts one), number of warp tasks and of kernel
- * launches one execution makes. */
+ * launches one execution makes.  flops_backward is the algorithmic count of
+ * a backward that forms the k x l rank-1 update of every term (2l + 6(n-1)
+ * + 2 + 18l + 8kl); the kernel's correction scheme avoids that update, so
+ * fp64_instr_backward (per term: column and correction updates, prefix and
+ * suffix products, accumulation; per chunk: the start from the high digits;
+ * per task: the lane contraction) is the count to compare with the FP64
+ * pipe.  fp64_instr_backward is filled in by the first backward call (zero
+ * before it), which also settles launches_backward. */
 typedef struct {
     int64_t permanents;
     int64_t terms;
@@ -287,6 +294,7 @@ typedef struct {
     int32_t lmax;
     int32_t reserved;
     double fp64_instr_forward;
+    double fp64_instr_backward;
 } pq_plan_stats;
 int pq_plan_get_stats(const pq_plan* plan, pq_plan_stats* out);
 

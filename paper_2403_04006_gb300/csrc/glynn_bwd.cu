@@ -43,7 +43,7 @@ constexpr int kLS = 33;
 __host__ __device__ inline int bwd_warp_smem_bytes(int kmax, int ld, int jb, int n2)
 {
     long bytes = 16L * (kmax * ld + ld + 3L * kLS * ld + 2L * kLS * n2 + kLS * (long)jb * ld) + 8L * 32 +
-                 4L * (kLS * (long)kmax + 16 + ld + kmax);
+                 8L * kLS * (long)kmax + 4L * (16 + ld + kmax);
     return (int)((bytes + 15) & ~15L);
 }
 
@@ -57,7 +57,7 @@ struct BwdSmem {
     double2* FULL;    // n2 x kLS
     double2* C;       // jb x ld x kLS
     double* wh;       // 32
-    int32_t* x;       // kmax x kLS
+    double* x;        // kmax x kLS: row multipliers x_i of each lane, then wh x_i
     int32_t* lowrow;  // 16
     int32_t* cm;      // ld
     int32_t* rowdig;  // kmax: low digit of each row, or -1
@@ -74,8 +74,8 @@ struct BwdSmem {
         FULL = PW + kLS * n2;
         C = FULL + kLS * n2;
         wh = reinterpret_cast<double*>(C + kLS * jb * ld);
-        x = reinterpret_cast<int32_t*>(wh + 32);
-        lowrow = x + kmax * kLS;
+        x = wh + 32;
+        lowrow = reinterpret_cast<int32_t*>(x + kmax * kLS);
         cm = lowrow + 16;
         rowdig = cm + ld;
     }
@@ -228,7 +228,7 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
             A[j * kLS] = make_double2(0.0, 0.0);
         }
         for (int i = 0; i < k; ++i)
-            sm.x[i * kLS + lane] = mv.rmul[i];
+            sm.x[i * kLS + lane] = (double)mv.rmul[i];
         uint64_t whigh_u = 1;
         int gpar = 0;
 #pragma unroll 1
@@ -247,7 +247,7 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
                 s.y = __fma_rn(coef, b.y, s.y);
                 S[j * kLS] = s;
             }
-            sm.x[row * kLS + lane] = mv.rmul[row] - 2 * g;
+            sm.x[row * kLS + lane] = (double)(mv.rmul[row] - 2 * g);
             if (g) {
                 whigh_u *= binom_u64(mv.dtop[d], g);
                 gpar += g;
@@ -301,28 +301,55 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
                     cv.y = __fma_rn(delta, av.y, cv.y);
                     Cd[j * kLS] = cv;
                 }
-                sm.x[row * kLS + lane] += (up > 0 ? -2 : 2);
                 if (((wk.radm1 >> (4 * d)) & 15u) > 1u)
                     wlow = (double)low_weight(wk, J);
             }
         }
         __syncwarp();
-        // lane-parallel contraction: entry e = (i, j) summed over the 32 lanes in order
+        // Contraction G_ij = sum_q wh_q (x_iq A_jq - C_{d(i) j q}) over the 32
+        // lanes q in order, as sum_q u_iq A_jq - V_{d(i) j} with u_iq = wh_q x_iq
+        // and V_dj = sum_q wh_q C_djq, so that each product is formed once.
+        // Low-digit rows end the chunk at the walk's final Gray value, which
+        // every lane shares.
+        for (int d = 0; d < J; ++d) {
+            const int g = (int)((wk.g >> (4 * d)) & 15u);
+            const int row = sm.lowrow[d];
+            sm.x[row * kLS + lane] = (double)(mv.rmul[row] - 2 * g);
+        }
+        {
+            const double whl = sm.wh[lane];
+            for (int i = 0; i < k; ++i)
+                sm.x[i * kLS + lane] *= whl;
+        }
+        double2* V = sm.P;  // the prefixes are no longer needed: J x ld entries
+        __syncwarp();
+        for (int e = lane; e < J * l; e += kWarp) {
+            const int d = e / l, j = e - d * l;
+            const double2* Cq = sm.C + (d * sm.ld + j) * kLS;
+            double vx = 0.0, vy = 0.0;
+            for (int q = 0; q < 32; ++q) {
+                const double2 cv = Cq[q];
+                vx = __fma_rn(sm.wh[q], cv.x, vx);
+                vy = __fma_rn(sm.wh[q], cv.y, vy);
+            }
+            V[d * sm.ld + j] = make_double2(vx, vy);
+        }
+        __syncwarp();
         for (int e = lane; e < kl; e += kWarp) {
             const int i = e / l, j = e - i * l;
             const int dg = sm.rowdig[i];
+            const double2* Aq = sm.A + j * kLS;
+            const double* uq = sm.x + i * kLS;
             double gx = 0.0, gy = 0.0;
             for (int q = 0; q < 32; ++q) {
-                const double2 av = sm.A[j * kLS + q];
-                const double xv = (double)sm.x[i * kLS + q];
-                double tx = xv * av.x, ty = xv * av.y;
-                if (dg >= 0) {
-                    const double2 cv = sm.C[(dg * sm.ld + j) * kLS + q];
-                    tx -= cv.x;
-                    ty -= cv.y;
-                }
-                gx = __fma_rn(sm.wh[q], tx, gx);
-                gy = __fma_rn(sm.wh[q], ty, gy);
+                const double2 av = Aq[q];
+                gx = __fma_rn(uq[q], av.x, gx);
+                gy = __fma_rn(uq[q], av.y, gy);
+            }
+            if (dg >= 0) {
+                const double2 v = V[dg * sm.ld + j];
+                gx = __dsub_rn(gx, v.x);
+                gy = __dsub_rn(gy, v.y);
             }
             slot[2 * e] = gx;
             slot[2 * e + 1] = gy;
@@ -473,11 +500,11 @@ cudaError_t bwd_prepare(int, int smem_bytes)
                                 smem_bytes);
 }
 
-cudaError_t bwd_launch_persistent(int ld, const BwdArgs& a, int kmax, int jb, int n2, int blocks,
-                                  int wpb, cudaStream_t st)
+cudaError_t bwd_launch_persistent(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end,
+                                  int kmax, int jb, int n2, int blocks, int wpb, cudaStream_t st)
 {
     const int smem = wpb * bwd_warp_smem_bytes(kmax, ld, jb, n2);
-    glynn_bwd_kernel<<<blocks, 32 * wpb, smem, st>>>(a, 0, a.ntasks, kmax, ld, jb, n2, 1);
+    glynn_bwd_kernel<<<blocks, 32 * wpb, smem, st>>>(a, t_begin, t_end, kmax, ld, jb, n2, 1);
     return cudaGetLastError();
 }
 

@@ -308,6 +308,23 @@ static double bwd_flops_per_term(const ItemPlan& it)
     return fwd_flops_per_term(it) + 18.0 * it.l + 8.0 * it.k * it.l;
 }
 
+// FP64 instructions of one backward term in glynn_bwd.cu: column-sum and
+// correction updates 4l; prefixes 4(l - 2); per middle column the product of
+// prefix and suffix, its accumulation and the suffix update, 10; the end
+// columns 4; per repeated column its powers and scaling.
+static double bwd_instr_per_term(const ItemPlan& it)
+{
+    if (it.n == 1)
+        return 2.0;
+    const int l = it.l;
+    double rep = 0.0;
+    for (int c : it.cmul)
+        if (c >= 2)
+            rep += 4.0 * (c - 1) + 5.0;
+    return 4.0 * l + 4.0 * std::max(l - 2, 0) + 10.0 * std::max(l - 2, 0) + 4.0 + rep +
+           (it.weighted ? 1.0 : 0.0);
+}
+
 static int default_log2_for(const pq_plan* P, const ItemPlan& it)
 {
     if (P->opts.chunk_log2 > 0)
@@ -909,6 +926,12 @@ extern "C" int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms
 // The backward pass keeps per-lane running sums for the low digits in shared
 // memory, so it uses its own, shorter chunks (at most kBwdMaxLowDigits low
 // digits, about 2^5 terms).
+// Product-column bounds of the backward launch classes: every permanent runs
+// in the launch of the smallest bound that holds its l, so its per-lane
+// workspace (column sums, accumulators, prefixes, corrections) is sized for
+// permanents like it rather than for the largest in the batch.
+static const int kBwdClassLd[] = {2, 4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40};
+
 static int ensure_backward(pq_plan* P)
 {
     if (P->bwd_ready)
@@ -918,26 +941,69 @@ static int ensure_backward(pq_plan* P)
     P->desc_bwd_h = P->desc_h;
     P->tasks_bwd_plain_h.clear();
     P->plain_first_bwd.assign(np + 1, 0);
+    P->bwd_class_of.assign(np, 0);
+    const int ncls = (int)(sizeof(kBwdClassLd) / sizeof(kBwdClassLd[0]));
+    std::vector<BwdClass> cls(ncls);
+    std::vector<int> cls_used(ncls, 0);
+    std::vector<double> cls_terms(ncls, 0.0), cls_nterms(ncls, 0.0);
+    for (int c = 0; c < ncls; ++c)
+        cls[c].ld = kBwdClassLd[c];
+    for (int64_t p = 0; p < np; ++p) {
+        const ItemPlan& it = items[p];
+        int c = 0;
+        while (c + 1 < ncls && kBwdClassLd[c] < it.l)
+            ++c;
+        P->bwd_class_of[p] = c;
+        cls_used[c] = 1;
+        cls[c].kmax = std::max(cls[c].kmax, it.k);
+        int c2 = 0;
+        for (int cm : it.cmul)
+            c2 += (cm >= 2) ? 1 : 0;
+        cls[c].n2 = std::max(cls[c].n2, c2);
+        if (!it.trivial) {
+            cls_terms[c] += (double)it.T;
+            cls_nterms[c] += (double)it.T * it.n;
+        }
+    }
+    // Low digits per chunk for each class: each digit costs every lane one row
+    // of corrections; fewer digits mean shorter chunks whose start-up (column
+    // sums from the high digits, about 2l(n - J) operations) is paid more
+    // often.  Take the J that maximises (share of the four warps per SM that
+    // saturate the FP64 pipe) x (share of the work that is per-term work).
+    for (int c = 0; c < ncls; ++c) {
+        if (!cls_used[c])
+            continue;
+        BwdClass& C = cls[c];
+        const double nbar = cls_terms[c] > 0 ? cls_nterms[c] / cls_terms[c] : 1.0;
+        double best = -1.0;
+        for (int J = kBwdMaxLowDigits; J >= 1; --J) {
+            const int per_warp = bwd_smem_bytes_for(C.kmax, C.ld, J, C.n2);
+            if (per_warp > 200 * 1024)
+                continue;
+            int wpb = 0, bps = 0;
+            launch_geometry_max(bwd_regs_per_thread(C.ld), per_warp, 8, wpb, bps);
+            const double warps = std::min(4.0, (double)(wpb * bps)) / 4.0;
+            const double per_term = 18.0 * C.ld + 8.0;
+            const double start = std::max(0.0, nbar - J) * 2.0 * C.ld / (double)(1 << J);
+            const double score = warps * per_term / (per_term + start);
+            if (score > best) {
+                best = score;
+                C.jb = J;
+                C.wpb = wpb;
+                C.blocks = std::max(1, P->num_sms * bps);
+            }
+        }
+        if (best < 0)
+            return fail(PQ_ERR_UNSUPPORTED, "backward shared memory for l <= %d too large", C.ld);
+    }
     std::vector<double> cost;
     std::vector<int64_t> gpart_off(np), gl_off(np);
     int64_t gpart = 0, gl = 0;
-    // Low digits per chunk: each costs every lane one row of corrections
-    // (ld complex) in shared memory; keep the per-warp workspace within a
-    // quarter of the SM so at least four warps (FP64 saturation) fit.
-    int n2max = 0;
-    for (const ItemPlan& it : items) {
-        int c2 = 0;
-        for (int c : it.cmul)
-            c2 += (c >= 2) ? 1 : 0;
-        n2max = std::max(n2max, c2);
-    }
-    int jcap = kBwdMaxLowDigits;
-    while (jcap > 1 &&
-           bwd_smem_bytes_for(P->kmax, P->lmax, jcap, n2max) > (227 * 1024) / 4)
-        --jcap;
+    double instr_b = 0.0;
     for (int64_t p = 0; p < np; ++p) {
         ItemPlan& it = items[p];
-        choose_chunks(it, kBwdChunkLog2, jcap);
+        const BwdClass& C = cls[P->bwd_class_of[p]];
+        choose_chunks(it, kBwdChunkLog2, std::max(C.jb, 1));
         PermDesc& D = P->desc_bwd_h[p];
         D.J = it.J;
         D.L = it.L;
@@ -960,15 +1026,47 @@ static int ensure_backward(pq_plan* P)
             P->tasks_bwd_plain_h.push_back(t);
             cost.push_back((double)it.L * fpt + 4.0 * kl);
         }
+        if (!it.trivial) {
+            // every lane of a task walks L terms and starts its chunk from the
+            // high digits; the task ends with the lane contraction
+            const double lane = (double)it.L * bwd_instr_per_term(it) +
+                                2.0 * it.l * (double)((int)it.drad.size() - it.J);
+            instr_b += (double)nt * (32.0 * lane + 32.0 * it.k + 64.0 * it.J * it.l + 66.0 * kl);
+        }
     }
     P->plain_first_bwd[np] = (int64_t)P->tasks_bwd_plain_h.size();
+    // batched order: class by class, longest task first within a class
     std::vector<int64_t> order(P->tasks_bwd_plain_h.size());
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        const int ca = P->bwd_class_of[P->tasks_bwd_plain_h[a].perm];
+        const int cb = P->bwd_class_of[P->tasks_bwd_plain_h[b].perm];
+        if (ca != cb)
+            return ca < cb;
+        return cost[a] > cost[b];
+    });
     P->tasks_bwd_batched_h.resize(order.size());
     for (size_t q = 0; q < order.size(); ++q)
         P->tasks_bwd_batched_h[q] = P->tasks_bwd_plain_h[order[q]];
+    P->bwd_classes.clear();
+    {
+        std::vector<int32_t> compact(ncls, -1);
+        int64_t q = 0;
+        const int64_t nt = (int64_t)order.size();
+        for (int c = 0; c < ncls; ++c) {
+            if (!cls_used[c])
+                continue;
+            BwdClass C = cls[c];
+            C.t_begin = q;
+            while (q < nt && P->bwd_class_of[P->tasks_bwd_batched_h[q].perm] == c)
+                ++q;
+            C.t_end = q;
+            compact[c] = (int32_t)P->bwd_classes.size();
+            P->bwd_classes.push_back(C);
+        }
+        for (int64_t p = 0; p < np; ++p)
+            P->bwd_class_of[p] = compact[P->bwd_class_of[p]];
+    }
 
     int rc;
     if ((rc = dev_upload(&P->desc_bwd_d, P->desc_bwd_h)) != PQ_OK)
@@ -1010,28 +1108,21 @@ static int ensure_backward(pq_plan* P)
         if ((rc = dev_upload(&P->bs_pos_d, pos)) != PQ_OK)
             return rc;
     }
-    // workspace sized by what the plan uses: low digits per chunk, repeated
-    // product columns
-    int jb = 0, n2 = 0;
-    for (const ItemPlan& it : items) {
-        jb = std::max(jb, it.J);
-        int c2 = 0;
-        for (int c : it.cmul)
-            c2 += (c >= 2) ? 1 : 0;
-        n2 = std::max(n2, c2);
+    int max_smem = 0, jb = 0, n2 = 0;
+    for (const BwdClass& C : P->bwd_classes) {
+        max_smem = std::max(max_smem, C.wpb * bwd_smem_bytes_for(C.kmax, C.ld, C.jb, C.n2));
+        jb = std::max(jb, C.jb);
+        n2 = std::max(n2, C.n2);
     }
     P->bwd_jb = jb;
     P->bwd_n2 = n2;
-    const int per_warp = bwd_smem_bytes_for(P->kmax, P->lmax, jb, n2);
-    if (per_warp > 200 * 1024)
-        return fail(PQ_ERR_UNSUPPORTED, "backward shared memory per warp %d too large", per_warp);
-    int wpb = 0, bps = 0;
-    launch_geometry(bwd_regs_per_thread(P->lmax), per_warp, 8, 8, wpb, bps);
-    P->bwd_wpb = wpb;
-    P->bwd_blocks = std::max(1, P->num_sms * bps);
-    cudaError_t e = bwd_prepare(P->lmax, wpb * per_warp);
+    cudaError_t e = bwd_prepare(P->lmax, max_smem);
     if (e != cudaSuccess)
         return fail(PQ_ERR_CUDA, "backward attribute setup failed: %s", cudaGetErrorString(e));
+    P->stats.launches_backward = (P->opts.method == PQ_METHOD_PLAIN)
+                                     ? np + 1
+                                     : (int64_t)P->bwd_classes.size() + 1;
+    P->stats.fp64_instr_backward = instr_b;
     P->bwd_ready = true;
     return PQ_OK;
 }
@@ -1063,17 +1154,25 @@ static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, co
     if (P->opts.method == PQ_METHOD_PLAIN) {
         a.tasks = P->tasks_bwd_plain_d;
         for (int64_t p = 0; p < P->nperm; ++p) {
-            e = bwd_launch_plain(P->lmax, a, P->plain_first_bwd[p], P->plain_first_bwd[p + 1],
-                                 P->kmax, P->bwd_jb, P->bwd_n2, P->bwd_wpb, st);
+            const BwdClass& C = P->bwd_classes[P->bwd_class_of[p]];
+            e = bwd_launch_plain(C.ld, a, P->plain_first_bwd[p], P->plain_first_bwd[p + 1],
+                                 C.kmax, C.jb, C.n2, C.wpb, st);
             if (e != cudaSuccess)
                 return fail(PQ_ERR_CUDA, "plain backward launch failed: %s", cudaGetErrorString(e));
         }
     } else {
+        // one persistent launch per class; the task queue counter restarts at
+        // zero for each (the per-permanent counters were cleared above)
         a.tasks = P->tasks_bwd_batched_d;
-        e = bwd_launch_persistent(P->lmax, a, P->kmax, P->bwd_jb, P->bwd_n2, P->bwd_blocks,
-                                  P->bwd_wpb, st);
-        if (e != cudaSuccess)
-            return fail(PQ_ERR_CUDA, "backward launch failed: %s", cudaGetErrorString(e));
+        for (size_t c = 0; c < P->bwd_classes.size(); ++c) {
+            const BwdClass& C = P->bwd_classes[c];
+            if (c > 0)
+                PQ_CUDA(cudaMemsetAsync(P->counters_d, 0, sizeof(int32_t), st));
+            e = bwd_launch_persistent(C.ld, a, C.t_begin, C.t_end, C.kmax, C.jb, C.n2, C.blocks,
+                                      C.wpb, st);
+            if (e != cudaSuccess)
+                return fail(PQ_ERR_CUDA, "backward launch failed: %s", cudaGetErrorString(e));
+        }
     }
     return PQ_OK;
 }

@@ -31,6 +31,33 @@ inline void launch_geometry(int regs_per_thread, int smem_per_warp, int want_wpb
         cap = 1;
     bps = want_bps < cap ? want_bps : cap;
 }
+// The (warps per block, blocks per SM) with the most resident warps, at most
+// want_wpb warps per block: registers as above; dynamic shared memory at most
+// 227 KB per block and 228 KB per SM including 1 KB the system reserves per
+// block.
+inline void launch_geometry_max(int regs_per_thread, int smem_per_warp, int want_wpb, int& wpb,
+                                int& bps)
+{
+    const int regs_warp = ((regs_per_thread * 32 + 255) / 256) * 256;
+    const int max_warps = 65536 / regs_warp > 0 ? 65536 / regs_warp : 1;
+    wpb = 1;
+    bps = 1;
+    int best = 0;
+    for (int w = 1; w <= want_wpb && w <= max_warps; ++w) {
+        const long block = (long)w * smem_per_warp;
+        if (block > 232448L)
+            break;
+        int b = (int)(233472L / (block + 1024L));
+        b = b < max_warps / w ? b : max_warps / w;
+        if (b < 1)
+            continue;
+        if (w * b >= best) {
+            best = w * b;
+            wpb = w;
+            bps = b;
+        }
+    }
+}
 cudaError_t fwd_prepare(int lmax, int smem_bytes);
 cudaError_t fwd_launch_persistent(int lmax, const ExecArgs& a, int kmax, int blocks, int wpb,
                                   cudaStream_t st);
@@ -58,8 +85,8 @@ int bwd_smem_bytes_for(int kmax, int lmax, int jb, int n2);
 constexpr int kBwdMaxLowDigits = 4;  // low digits the backward workspace holds
 constexpr int kBwdChunkLog2 = 4;     // backward chunks of at most 2^4 terms
 cudaError_t bwd_prepare(int lmax, int smem_bytes);
-cudaError_t bwd_launch_persistent(int lmax, const BwdArgs& a, int kmax, int jb, int n2, int blocks,
-                                  int wpb, cudaStream_t st);
+cudaError_t bwd_launch_persistent(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end,
+                                  int kmax, int jb, int n2, int blocks, int wpb, cudaStream_t st);
 cudaError_t bwd_launch_plain(int lmax, const BwdArgs& a, int64_t t_begin, int64_t t_end,
                              int kmax, int jb, int n2, int wpb, cudaStream_t st);
 

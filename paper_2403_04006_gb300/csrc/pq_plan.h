@@ -27,6 +27,13 @@ struct ItemPlan {
     double norm = 1.0;
 };
 
+// One backward launch: the permanents whose product side fits ld columns,
+// with the shared-memory layout sized for them.
+struct BwdClass {
+    int ld = 1, kmax = 1, jb = 0, n2 = 0, wpb = 1, blocks = 1;
+    int64_t t_begin = 0, t_end = 0;  // range in the batched backward task list
+};
+
 struct DeviceBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -76,6 +83,8 @@ struct pq_plan {
     std::vector<pqi::PermDesc> desc_bwd_h;
     std::vector<pqi::Task> tasks_bwd_plain_h, tasks_bwd_batched_h;
     std::vector<int64_t> plain_first_bwd;
+    std::vector<pqi::BwdClass> bwd_classes;
+    std::vector<int32_t> bwd_class_of;  // class of each permanent
     pqi::PermDesc* desc_bwd_d = nullptr;
     pqi::Task* tasks_bwd_plain_d = nullptr;
     pqi::Task* tasks_bwd_batched_d = nullptr;
