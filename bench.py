@@ -496,6 +496,20 @@ def extra_measurements(args, dev, stream, flush, peak_tflops, fp64_lane_ops):
     api.bs_sample(Us, s8, order, unif)
     secs = time.perf_counter() - t0
     res["sampler_m16_n8"] = {"samples": 2000, "s": secs, "samples_per_s": 2000 / secs}
+    # lossy boson sampling (Sec. 3.2.4): m = 10 Haar factors V, W, transmissions
+    # eta ~ U[0.5, 0.95], 5 photons in modes 0..4, every output pattern with at
+    # most 5 photons (3003 patterns, 42504 permanents of the 20-mode dilation);
+    # one synchronous call, planning included
+    rl = W.rng_for(10)
+    Vl, Wl = W.haar_unitary(10, rl), W.haar_unitary(10, rl)
+    etal = rl.uniform(0.5, 0.95, 10)
+    sl = np.zeros(10, dtype=np.int32)
+    sl[:5] = 1
+    tl = np.concatenate([W.compositions(k, 10) for k in range(6)])
+    Vd, Wd, etad = (torch.from_numpy(x).to(dev) for x in (Vl, Wl, etal))
+    ms = timed(lambda: api.bs_probs_lossy(Vd, etad, Wd, sl, tl, stream=stream), 3)
+    res["lossy_m10_n5"] = {"patterns": int(tl.shape[0]), "permanents": 42504, "ms": ms,
+                           "patterns_per_s": tl.shape[0] / ms * 1e3}
     # batched boson sampling, m = 24, 4096 patterns
     U, s, t = W.bs_batched()
     Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))

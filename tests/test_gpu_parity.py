@@ -290,6 +290,27 @@ def test_permanent_backward_vs_minors(dev):
             assert np.abs(got - ref).max() <= TOLG * max(np.abs(ref).max(), 1e-300)
 
 
+def test_permanent_backward_large_product_sides(dev):
+    """Backward launch classes for wide product sides (l up to 15) and narrow
+    ones in one batch, both methods, against the Laplace minors."""
+    rng = np.random.default_rng(406)
+    items = random_items(3, 13, 15, rng, maxpart=1)   # every column distinct: l = n
+    items += random_items(3, 14, 18, rng, maxpart=2)
+    items += random_items(6, 2, 6, rng)
+    pb = W.pack_batch(items)
+    db = api.DeviceBatch(pb, dev)
+    gout = (rng.standard_normal(pb.batch) + 1j * rng.standard_normal(pb.batch))
+    refs = [gout[b] * np.conj(O.perm_grad(B, r, c)) for b, (B, r, c) in enumerate(items)]
+    for method in ("batched", "plain"):
+        plan = api.Plan.for_batch(pb, method=method)
+        g = api.permanent_backward(db, torch.from_numpy(gout).to(dev), plan).cpu().numpy()
+        assert plan.stats()["fp64_instr_backward"] > 0
+        for b, (B, r, c) in enumerate(items):
+            o = int(pb.mat_off[b])
+            got = g[o:o + B.size].reshape(B.shape)
+            assert np.abs(got - refs[b]).max() <= TOLG * np.abs(refs[b]).max()
+
+
 def test_permanent_gradcheck(dev):
     rng = np.random.default_rng(505)
     items = random_items(4, 2, 5, rng)
