@@ -8,9 +8,18 @@
 // photon at a time: at step k (k = 1 .. n), with r_1 .. r_{k-1} already drawn,
 //   w_i = |per(A[{r_1 .. r_{k-1}, i}, 1 .. k])|^2,   i = 0 .. m-1,
 // and r_k is drawn with probability w_i / sum w.  The multiset {r_1 .. r_n}
-// is a sample of Eq. (BS_prob).  Rows r may repeat, so every step is a batch
-// of permanents with repeated rows (and repeated columns when s_j > 1): one
-// persistent launch per step for all samples at once.
+// is a sample of Eq. (BS_prob).
+//
+// Expanding each permanent along its last row,
+//   per(A[{r, i}, 1 .. k]) = sum_{j <= k} A[i, j] per(M_j),
+//   M_j = A[{r_1 .. r_{k-1}}, {1 .. k} \ {j}],
+// so a step needs k permanents of size k - 1 per sample, not m of size k.
+// Every step runs on the device without the host: a gather kernel builds the
+// minors from the rows drawn so far (repeated rows stay separate rows, so
+// all minors of a step have one shape and the step's plan is made once,
+// before the first step), one persistent launch evaluates them, a kernel
+// forms the m weights of every sample and draws its photon.  The host reads
+// the drawn modes back once, after the last step.
 //
 // Random numbers are inputs (column orders and one uniform per photon), so
 // a caller can reproduce a run exactly.  Selection rule: with the weights
@@ -26,16 +35,55 @@
 
 namespace pqi {
 
-__global__ void sample_select_kernel(const double* w, int64_t B, int m, const double* u,
-                                     int32_t* chosen)
+// Minors of step k: item (b, j) is A_b[{r_1 .. r_{k-1}}, {c_0 .. c_{k-1}} \ {c_j}],
+// (k-1) x (k-1) row-major at (b k + j) (k-1)^2.  cols[b n + q] is the input
+// mode of sample b's q-th photon column, drawn[b n + p] its p-th drawn mode.
+__global__ void sampler_gather_kernel(const double2* U, int m, int n, int k, int64_t nsamples,
+                                      const int32_t* cols, const int32_t* drawn, double2* mats)
 {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B;
+    const int d = k - 1;
+    const int64_t total = nsamples * k * d * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t item = e / (d * d);
+        const int rem = (int)(e - item * d * d);
+        const int p = rem / d, q = rem - p * d;
+        const int64_t b = item / k;
+        const int j = (int)(item - b * k);
+        const int qq = q < j ? q : q + 1;
+        const int row = drawn[b * n + p];
+        const int col = cols[b * n + qq];
+        mats[e] = U[(int64_t)row * m + col];
+    }
+}
+
+// Weights of step k, w_i = |sum_j U[i, c_j] per_j|^2 (per_j = 1 for k = 1),
+// and the draw: the first mode whose running weight sum exceeds u * total,
+// else the last mode with a positive weight; a sample whose weights are all
+// zero records an error and draws mode 0 so that later steps stay in bounds.
+__global__ void sampler_step_kernel(const double2* U, int m, int n, int k, int64_t nsamples,
+                                    const int32_t* cols, const double2* per, const double* uniforms,
+                                    double* w, int32_t* drawn, int32_t* err)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nsamples;
          b += (int64_t)gridDim.x * blockDim.x) {
-        const double* wb = w + b * m;
+        double* wb = w + b * m;
         double tot = 0.0;
-        for (int i = 0; i < m; ++i)
-            tot += wb[i];
-        const double thr = u[b] * tot;
+        for (int i = 0; i < m; ++i) {
+            double2 z = make_double2(0.0, 0.0);
+            for (int j = 0; j < k; ++j) {
+                const double2 a = U[(int64_t)i * m + cols[b * n + j]];
+                const double2 pj = (k == 1) ? make_double2(1.0, 0.0) : per[b * k + j];
+                z.x = __fma_rn(a.x, pj.x, z.x);
+                z.x = __fma_rn(-a.y, pj.y, z.x);
+                z.y = __fma_rn(a.x, pj.y, z.y);
+                z.y = __fma_rn(a.y, pj.x, z.y);
+            }
+            const double wi = z.x * z.x + z.y * z.y;
+            wb[i] = wi;
+            tot += wi;
+        }
+        const double thr = uniforms[b * n + (k - 1)] * tot;
         double run = 0.0;
         int pick = -1, last = -1;
         for (int i = 0; i < m; ++i) {
@@ -45,7 +93,13 @@ __global__ void sample_select_kernel(const double* w, int64_t B, int m, const do
             if (pick < 0 && run > thr)
                 pick = i;
         }
-        chosen[b] = pick >= 0 ? pick : last;
+        if (pick < 0)
+            pick = last;
+        if (pick < 0) {
+            atomicExch(err, 1);
+            pick = 0;
+        }
+        drawn[b * n + (k - 1)] = pick;
     }
 }
 
@@ -62,16 +116,17 @@ extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_oc
     if (m <= 0 || m > PQ_MAX_DIM || nsamples < 0)
         return report(PQ_ERR_ARG, "bad sizes");
     int n = 0;
-    std::vector<int32_t> cols;  // input mode of each photon column
+    std::vector<int32_t> modes;  // input mode of each photon column
     for (int j = 0; j < m; ++j) {
         if (input_occ[j] < 0)
             return report(PQ_ERR_ARG, "negative input occupation");
         for (int q = 0; q < input_occ[j]; ++q)
-            cols.push_back(j);
+            modes.push_back(j);
         n += input_occ[j];
     }
     if (n > PQ_MAX_N)
         return report(PQ_ERR_UNSUPPORTED, "too many photons");
+    std::vector<int32_t> cols((size_t)nsamples * n);
     for (int64_t b = 0; b < nsamples; ++b) {  // every column order is a permutation
         std::vector<char> seen(n, 0);
         for (int q = 0; q < n; ++q) {
@@ -79,83 +134,112 @@ extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_oc
             if (c < 0 || c >= n || seen[c])
                 return report(PQ_ERR_ARG, "col_order row is not a permutation of 0 .. n-1");
             seen[c] = 1;
+            cols[(size_t)b * n + q] = modes[c];
         }
     }
     for (int64_t b = 0; b < nsamples * n; ++b)
         if (!(uniforms[b] >= 0.0 && uniforms[b] < 1.0))
             return report(PQ_ERR_ARG, "uniforms must lie in [0, 1)");
-    std::vector<int32_t> occ((size_t)nsamples * m, 0);
-    if (nsamples == 0 || n == 0) {
-        for (size_t e = 0; e < occ.size(); ++e)
-            samples[e] = 0;
+    for (int64_t e = 0; e < nsamples * m; ++e)
+        samples[e] = 0;
+    if (nsamples == 0 || n == 0)
         return PQ_OK;
+    if (nsamples > (int64_t(1) << 40) / ((int64_t)n * n * n + m))
+        return report(PQ_ERR_UNSUPPORTED, "sampler workspace too large");
+
+    // one plan per step k >= 2: nsamples * k minors of size k - 1, every
+    // multiplicity one, item (b, j) at element offset (b k + j) (k-1)^2
+    std::vector<pq_plan*> plans(n + 1, nullptr);
+    int rc = PQ_OK;
+    for (int k = 2; k <= n && rc == PQ_OK; ++k) {
+        const int d = k - 1;
+        const int64_t B = nsamples * k;
+        std::vector<int64_t> mat_off(B), zero_off(B, 0);
+        std::vector<int32_t> dim(B, d), ones(d, 1);
+        for (int64_t q = 0; q < B; ++q)
+            mat_off[q] = q * d * d;
+        pq_batch_sizes sz;
+        sz.batch = B;
+        sz.mat_off = mat_off.data();
+        sz.k = dim.data();
+        sz.l = dim.data();
+        sz.row_mult = ones.data();
+        sz.row_off = zero_off.data();
+        sz.col_mult = ones.data();
+        sz.col_off = zero_off.data();
+        rc = pq_plan_create(&sz, nullptr, &plans[k]);
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t B = nsamples * m;
+    const int64_t Bmax = nsamples * n;
+    const int64_t mat_elems = std::max<int64_t>(1, nsamples * n * (int64_t)(n - 1) * (n - 1));
+    double2 *mats_d = nullptr, *per_d = nullptr;
     double *w_d = nullptr, *u_d = nullptr;
-    int32_t* pick_d = nullptr;
-    if (cudaMalloc((void**)&w_d, B * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&u_d, nsamples * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&pick_d, nsamples * sizeof(int32_t)) != cudaSuccess) {
-        cudaFree(w_d);
-        cudaFree(u_d);
-        cudaFree(pick_d);
-        return report(PQ_ERR_NOMEM, "sampler workspace allocation failed");
-    }
-    std::vector<int32_t> t((size_t)B * m), s((size_t)B * m), pick(nsamples);
-    std::vector<double> u(nsamples);
-    int rc = PQ_OK;
+    int32_t *cols_d = nullptr, *drawn_d = nullptr, *err_d = nullptr;
+    if (rc == PQ_OK &&
+        (cudaMalloc((void**)&mats_d, mat_elems * sizeof(double2)) != cudaSuccess ||
+         cudaMalloc((void**)&per_d, Bmax * sizeof(double2)) != cudaSuccess ||
+         cudaMalloc((void**)&w_d, nsamples * m * sizeof(double)) != cudaSuccess ||
+         cudaMalloc((void**)&u_d, nsamples * n * sizeof(double)) != cudaSuccess ||
+         cudaMalloc((void**)&cols_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
+         cudaMalloc((void**)&drawn_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
+         cudaMalloc((void**)&err_d, sizeof(int32_t)) != cudaSuccess))
+        rc = report(PQ_ERR_NOMEM, "sampler workspace allocation failed");
+    if (rc == PQ_OK &&
+        (cudaMemcpyAsync(u_d, uniforms, nsamples * n * sizeof(double), cudaMemcpyHostToDevice,
+                         st) != cudaSuccess ||
+         cudaMemcpyAsync(cols_d, cols.data(), nsamples * n * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemsetAsync(drawn_d, 0, nsamples * n * sizeof(int32_t), st) != cudaSuccess ||
+         cudaMemsetAsync(err_d, 0, sizeof(int32_t), st) != cudaSuccess))
+        rc = report(PQ_ERR_CUDA, "sampler upload failed");
+    const unsigned sblocks =
+        (unsigned)std::min<int64_t>((nsamples + 127) / 128, 4096);
     for (int k = 1; k <= n && rc == PQ_OK; ++k) {
-        // item (b, i): rows = drawn photons of sample b plus mode i; columns =
-        // the input modes of sample b's first k photon columns
-        for (int64_t b = 0; b < nsamples; ++b) {
-            std::vector<int32_t> sc(m, 0);
-            for (int q = 0; q < k; ++q)
-                sc[cols[col_order[b * n + q]]] += 1;
-            for (int i = 0; i < m; ++i) {
-                int32_t* tb = t.data() + (size_t)(b * m + i) * m;
-                int32_t* sb = s.data() + (size_t)(b * m + i) * m;
-                for (int a = 0; a < m; ++a) {
-                    tb[a] = occ[(size_t)b * m + a];
-                    sb[a] = sc[a];
-                }
-                tb[i] += 1;
-            }
-            u[b] = uniforms[b * n + (k - 1)];
-        }
-        pq_plan* P = nullptr;
-        rc = plan_create_occupations(m, t, s, B, &P);
-        if (rc != PQ_OK)
-            break;
-        rc = plan_run_forward(P, U, nullptr, w_d, st);
-        if (rc == PQ_OK) {
-            if (cudaMemcpyAsync(u_d, u.data(), nsamples * sizeof(double), cudaMemcpyHostToDevice,
-                                st) != cudaSuccess)
-                rc = report(PQ_ERR_CUDA, "uniform upload failed");
-        }
-        if (rc == PQ_OK) {
-            const unsigned blocks = (unsigned)((nsamples + 127) / 128 < 1024 ? (nsamples + 127) / 128 : 1024);
-            sample_select_kernel<<<blocks, 128, 0, st>>>(w_d, nsamples, m, u_d, pick_d);
-            if (cudaGetLastError() != cudaSuccess ||
-                cudaMemcpyAsync(pick.data(), pick_d, nsamples * sizeof(int32_t),
-                                cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                rc = report(PQ_ERR_CUDA, "sampling step failed");
-        }
-        pq_plan_destroy(P);
-        for (int64_t b = 0; b < nsamples && rc == PQ_OK; ++b) {
-            if (pick[b] < 0) {
-                rc = report(PQ_ERR_ARG, "all weights of a sampling step are zero");
+        if (k >= 2) {
+            const int64_t total = nsamples * k * (int64_t)(k - 1) * (k - 1);
+            const unsigned gblocks = (unsigned)std::min<int64_t>((total + 255) / 256, 65536);
+            sampler_gather_kernel<<<gblocks, 256, 0, st>>>(
+                reinterpret_cast<const double2*>(U), m, n, k, nsamples, cols_d, drawn_d, mats_d);
+            if (cudaGetLastError() != cudaSuccess) {
+                rc = report(PQ_ERR_CUDA, "minor gather failed");
                 break;
             }
-            occ[(size_t)b * m + pick[b]] += 1;
+            rc = plan_run_forward(plans[k], mats_d, per_d, nullptr, st);
+            if (rc != PQ_OK)
+                break;
         }
+        sampler_step_kernel<<<sblocks, 128, 0, st>>>(reinterpret_cast<const double2*>(U), m, n, k,
+                                                     nsamples, cols_d, per_d, u_d, w_d, drawn_d,
+                                                     err_d);
+        if (cudaGetLastError() != cudaSuccess)
+            rc = report(PQ_ERR_CUDA, "sampling step failed");
     }
+    std::vector<int32_t> drawn((size_t)nsamples * n);
+    int32_t err = 0;
+    if (rc == PQ_OK &&
+        (cudaMemcpyAsync(drawn.data(), drawn_d, nsamples * n * sizeof(int32_t),
+                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaMemcpyAsync(&err, err_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+             cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+        rc = report(PQ_ERR_CUDA, "sampler read-back failed");
+    if (rc == PQ_OK && err)
+        rc = report(PQ_ERR_ARG, "all weights of a sampling step are zero");
+    if (rc != PQ_OK)
+        cudaStreamSynchronize(st);
+    cudaFree(mats_d);
+    cudaFree(per_d);
     cudaFree(w_d);
     cudaFree(u_d);
-    cudaFree(pick_d);
+    cudaFree(cols_d);
+    cudaFree(drawn_d);
+    cudaFree(err_d);
+    for (pq_plan* P : plans)
+        if (P)
+            pq_plan_destroy(P);
     if (rc == PQ_OK)
-        for (size_t e = 0; e < occ.size(); ++e)
-            samples[e] = occ[e];
+        for (int64_t b = 0; b < nsamples; ++b)
+            for (int q = 0; q < n; ++q)
+                samples[b * m + drawn[(size_t)b * n + q]] += 1;
     return rc;
 }
