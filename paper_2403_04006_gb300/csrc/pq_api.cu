@@ -1455,6 +1455,13 @@ int plan_run_forward(pq_plan* P, const void* src, void* amps, double* probs, cud
     return run_forward_raw(P, src, amps, probs, st);
 }
 
+int plan_prepare_forward(pq_plan* P)
+{
+    const cudaError_t e = fwd_prepare(P->lmax, P->wpb * fwd_smem_per_warp(P->kmax, P->lmax));
+    return e == cudaSuccess ? PQ_OK : fail(PQ_ERR_CUDA, "kernel attribute setup failed: %s",
+                                            cudaGetErrorString(e));
+}
+
 int report(int code, const char* msg) { return fail(code, "%s", msg); }
 
 }  // namespace pqi

@@ -112,4 +112,6 @@ namespace pqi {
 int plan_create_occupations(int32_t m, const std::vector<int32_t>& t, const std::vector<int32_t>& s,
                             int64_t B, pq_plan** out);
 int plan_run_forward(pq_plan* P, const void* src, void* amps, double* probs, cudaStream_t st);
+// Raise the forward kernel's shared-memory limit to what plan P launches with.
+int plan_prepare_forward(pq_plan* P);
 }  // namespace pqi

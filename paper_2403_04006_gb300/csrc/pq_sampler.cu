@@ -27,6 +27,10 @@
 // u * total (the last mode with a positive weight if rounding leaves none).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pq.h"
@@ -148,27 +152,56 @@ extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_oc
         return report(PQ_ERR_UNSUPPORTED, "sampler workspace too large");
 
     // one plan per step k >= 2: nsamples * k minors of size k - 1, every
-    // multiplicity one, item (b, j) at element offset (b k + j) (k-1)^2
+    // multiplicity one, item (b, j) at element offset (b k + j) (k-1)^2.  The
+    // plans are independent, so host threads build them side by side.
     std::vector<pq_plan*> plans(n + 1, nullptr);
-    int rc = PQ_OK;
-    for (int k = 2; k <= n && rc == PQ_OK; ++k) {
-        const int d = k - 1;
-        const int64_t B = nsamples * k;
-        std::vector<int64_t> mat_off(B), zero_off(B, 0);
-        std::vector<int32_t> dim(B, d), ones(d, 1);
-        for (int64_t q = 0; q < B; ++q)
-            mat_off[q] = q * d * d;
-        pq_batch_sizes sz;
-        sz.batch = B;
-        sz.mat_off = mat_off.data();
-        sz.k = dim.data();
-        sz.l = dim.data();
-        sz.row_mult = ones.data();
-        sz.row_off = zero_off.data();
-        sz.col_mult = ones.data();
-        sz.col_off = zero_off.data();
-        rc = pq_plan_create(&sz, nullptr, &plans[k]);
+    std::vector<int> prc(n + 1, PQ_OK);
+    std::vector<std::string> perr(n + 1);
+    std::atomic<int> next_k(2);
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess)
+        return report(PQ_ERR_CUDA, "no current CUDA device");
+    auto worker = [&]() {
+        cudaSetDevice(device);  // a new host thread starts on device 0
+        for (int k = next_k++; k <= n; k = next_k++) {
+            const int d = k - 1;
+            const int64_t B = nsamples * k;
+            std::vector<int64_t> mat_off(B), zero_off(B, 0);
+            std::vector<int32_t> dim(B, d), ones(d, 1);
+            for (int64_t q = 0; q < B; ++q)
+                mat_off[q] = q * d * d;
+            pq_batch_sizes sz;
+            sz.batch = B;
+            sz.mat_off = mat_off.data();
+            sz.k = dim.data();
+            sz.l = dim.data();
+            sz.row_mult = ones.data();
+            sz.row_off = zero_off.data();
+            sz.col_mult = ones.data();
+            sz.col_off = zero_off.data();
+            prc[k] = pq_plan_create(&sz, nullptr, &plans[k]);
+            if (prc[k] != PQ_OK)
+                perr[k] = pq_last_error();
+        }
+    };
+    {
+        const int nthreads = std::max(1, std::min(n - 1, 16));
+        std::vector<std::thread> pool;
+        for (int q = 1; q < nthreads; ++q)
+            pool.emplace_back(worker);
+        worker();
+        for (std::thread& th : pool)
+            th.join();
     }
+    int rc = PQ_OK;
+    for (int k = 2; k <= n && rc == PQ_OK; ++k)
+        if (prc[k] != PQ_OK)
+            rc = report(prc[k], perr[k].c_str());
+    // Plans made side by side may have raised the kernel's shared-memory
+    // limit out of order: raise it once more for each, in turn.
+    for (int k = 2; k <= n && rc == PQ_OK; ++k)
+        if (plan_prepare_forward(plans[k]) != PQ_OK)
+            rc = report(PQ_ERR_CUDA, "kernel attribute setup failed");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t Bmax = nsamples * n;
     const int64_t mat_elems = std::max<int64_t>(1, nsamples * n * (int64_t)(n - 1) * (n - 1));
