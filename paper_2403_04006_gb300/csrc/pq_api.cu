@@ -752,7 +752,14 @@ static int run_forward_raw(pq_plan* P, const void* src, void* amps, double* prob
 
 static int run_forward(pq_plan* P, const void* src, void* amps, double* probs, cudaStream_t st)
 {
-    const bool graph = P->opts.use_graph && P->opts.method == PQ_METHOD_BATCHED && st != nullptr;
+    bool graph = P->opts.use_graph && P->opts.method == PQ_METHOD_BATCHED && st != nullptr;
+    if (graph) {
+        // Inside a caller's stream capture the launch is simply recorded into
+        // the caller's graph (a capture cannot begin on a capturing stream).
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        PQ_CUDA(cudaStreamIsCapturing(st, &cs));
+        graph = (cs == cudaStreamCaptureStatusNone);
+    }
     if (!graph)
         return run_forward_raw(P, src, amps, probs, st);
     const void* key[4] = {src, amps, probs, st};

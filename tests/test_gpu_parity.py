@@ -416,3 +416,48 @@ def test_paper_repeated_permanents(dev, method):
     got, plan = gpu_perms(pb, dev, method)
     assert plan.stats()["terms"] == sum(2 * 3 ** (k - 1) for k in range(4, 15))
     assert rel_err(got, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_plans_run_inside_a_callers_graph_capture(dev, use_graph):
+    """An executed plan allocates nothing, reads no host memory and does not
+    synchronise, so a caller can capture it (forward, boson-sampling
+    probabilities and, after the first backward call, the backward) into its
+    own CUDA graph; replays follow new input values."""
+    rng = np.random.default_rng(707)
+    items = random_items(40, 2, 9, rng)
+    pb = W.pack_batch(items)
+    db = api.DeviceBatch(pb, dev)
+    plan = api.Plan.for_batch(pb, use_graph=use_graph)
+    out = torch.empty(pb.batch, dtype=torch.complex128, device=dev)
+    gout = torch.ones(pb.batch, dtype=torch.complex128, device=dev)
+    api.permanent_backward(db, gout, plan)  # plans the backward outside the capture
+    U, s, t = W.bs_small()
+    Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))
+    bplan = api.Plan.for_bs(8, s, t, use_graph=use_graph)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        api.permanent_batched(db, plan, out=out)
+        grad = api.permanent_backward(db, gout, plan)
+        probs, _ = api.bs_probs(Ud, sd, td, bplan)
+    for rep in range(2):
+        new = (rng.standard_normal(pb.mats.shape) + 1j * rng.standard_normal(pb.mats.shape)) * 0.3
+        db.mats.copy_(torch.from_numpy(new))
+        Ud.copy_(torch.from_numpy(W.haar_unitary(8, rng)))
+        g.replay()
+        torch.cuda.synchronize()
+        ref_out = api.permanent_batched(db, plan).cpu().numpy()
+        ref_grad = api.permanent_backward(db, gout, plan).cpu().numpy()
+        ref_p, _ = api.bs_probs(Ud, sd, td, bplan)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref_out)
+        assert np.array_equal(grad.cpu().numpy(), ref_grad)
+        assert np.array_equal(probs.cpu().numpy(), ref_p.cpu().numpy())
+        # and the values are the permanents of the new matrices
+        for b in range(0, pb.batch, 7):
+            B, r, c = items[b]
+            o = int(pb.mat_off[b])
+            Bn = new[o:o + B.size].reshape(B.shape)
+            ref = O.perm_ryser(Bn, r, c, gold=True)
+            assert abs(ref_out[b] - ref) <= TOL * max(abs(ref), 1e-300)
