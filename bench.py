@@ -379,6 +379,8 @@ def bench_ours(args):
                      "frac_of_probe": achieved_tflops / (peak_flops / 1e12),
                      "fp64_pipe_frac": st["fp64_instr_forward"] / (ms_mean * 1e-3)
                                        / (2.0 * sms * clock_mhz * 1e6),
+                     "fp64_pipe_frac_executed": st["fp64_instr_forward_executed"]
+                                                / (ms_mean * 1e-3) / (2.0 * sms * clock_mhz * 1e6),
                      "flops_per_step": st["flops_forward"],
                      "fp64_instr_per_step": st["fp64_instr_forward"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

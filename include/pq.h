@@ -282,7 +282,12 @@ int pq_autotune(pq_plan* plan, const pq_batch* b, const pq_c128* U, void* stream
  * suffix products, accumulation; per chunk: the start from the high digits;
  * per task: the lane contraction) is the count to compare with the FP64
  * pipe.  fp64_instr_backward is filled in by the first backward call (zero
- * before it), which also settles launches_backward. */
+ * before it), which also settles launches_backward.
+ * fp64_instr_forward_executed adds what the forward executes besides the
+ * terms, counted per lane: the lanes of a task without a chunk (they walk
+ * with the others), each chunk's start from its high digits, the fold and
+ * scaling of each chunk's sum, the per-task lane reduction and the
+ * per-permanent combination of task partials. */
 typedef struct {
     int64_t permanents;
     int64_t terms;
@@ -295,6 +300,7 @@ typedef struct {
     int32_t reserved;
     double fp64_instr_forward;
     double fp64_instr_backward;
+    double fp64_instr_forward_executed;
 } pq_plan_stats;
 int pq_plan_get_stats(const pq_plan* plan, pq_plan_stats* out);
 

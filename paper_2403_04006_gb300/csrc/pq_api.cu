@@ -420,7 +420,7 @@ static int schedule_and_upload(pq_plan* P)
     P->plain_first.assign(np + 1, 0);
     std::vector<double> task_cost;
     int32_t slot = 0;
-    double flops_f = 0.0, flops_b = 0.0, instr_f = 0.0;
+    double flops_f = 0.0, flops_b = 0.0, instr_f = 0.0, instr_fx = 0.0;
     int64_t terms = 0;
     for (int64_t p = 0; p < np; ++p) {
         ItemPlan& it = P->items[p];
@@ -474,6 +474,15 @@ static int schedule_and_upload(pq_plan* P)
             flops_f += (double)it.T * fpt;
             instr_f += (double)it.T * fwd_instr_per_term(it);
             flops_b += (double)it.T * bwd_flops_per_term(it);
+            // per task, every lane: L terms, the chunk start ((ndig - J) row
+            // updates of 2l), the chunk's fold and scaling (28) and the lane
+            // tree (92); per permanent with several tasks, the partials'
+            // double-double sum (20 per task and lane) and one more tree
+            const double lane = (double)it.L * fwd_instr_per_term(it) +
+                                2.0 * it.l * (double)((int)it.drow.size() - it.J) + 28.0 + 92.0;
+            instr_fx += (double)nt * 32.0 * lane;
+            if (nt > 1)
+                instr_fx += 32.0 * (20.0 * (double)((nt + kWarp - 1) / kWarp) + 92.0);
         }
         if (slot < 0)
             return fail(PQ_ERR_UNSUPPORTED, "too many tasks");
@@ -504,6 +513,7 @@ static int schedule_and_upload(pq_plan* P)
     P->stats.flops_forward = flops_f;
     P->stats.flops_backward = flops_b;
     P->stats.fp64_instr_forward = instr_f;
+    P->stats.fp64_instr_forward_executed = instr_fx;
     P->stats.tasks = (int64_t)P->tasks_plain_h.size();
     P->stats.launches_forward = (P->opts.method == PQ_METHOD_PLAIN) ? np : 1;
     P->stats.launches_backward = (P->opts.method == PQ_METHOD_PLAIN) ? np + 1 : 2;

@@ -52,7 +52,8 @@ class pq_plan_stats(ctypes.Structure):
                 ("flops_backward", ctypes.c_double), ("tasks", _i64),
                 ("launches_forward", _i64), ("launches_backward", _i64), ("lmax", _i32),
                 ("reserved", _i32), ("fp64_instr_forward", ctypes.c_double),
-                ("fp64_instr_backward", ctypes.c_double)]
+                ("fp64_instr_backward", ctypes.c_double),
+                ("fp64_instr_forward_executed", ctypes.c_double)]
 
 
 # name -> (restype, argtypes)
