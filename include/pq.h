@@ -107,7 +107,10 @@ typedef struct {
                                 chunk of about 2^chunk_log2 terms for every permanent     */
     int32_t warps_per_block; /* 0: default (8)                                            */
     int32_t blocks_per_sm;   /* 0: default (1)                                            */
-    int32_t reserved[3];
+    int32_t shard_index;     /* with shard_count > 1: this plan covers shard shard_index  */
+    int32_t shard_count;     /* of the warp tasks of every permanent (see
+                                pq_permanent_partials); 0 or 1: no sharding              */
+    int32_t reserved;
 } pq_plan_options;
 
 /* Opaque plan: the host-side schedule of one batch shape (which side of each
@@ -143,6 +146,22 @@ int pq_plan_destroy(pq_plan* plan);
  * the sizes to the host, plans, runs the batched method and synchronises
  * `stream` before returning (convenience path; it allocates). */
 int pq_permanent_batched(const pq_batch* b, pq_c128* out, pq_plan* plan, void* stream);
+
+/* Partial sums of a sharded permanent batch: the warp tasks of every
+ * permanent (runs of 32 Gray-code chunks) are cut into shard_count contiguous
+ * ranges, and a plan made with shard_index = r covers range r.  One rank (or
+ * one GPU) per shard runs this call; partials[4p .. 4p+3] receives its
+ * double-double sum (re hi, re lo, im hi, im lo) of the Glynn terms of
+ * permanent p, WITHOUT the factor 2^{-(n-1)}.  Adding the shards' partials
+ * (in double-double, in shard order) and scaling by 2^{-(n-1)} gives per; a
+ * permanent with n = 0 contributes 1 on exactly one shard and 0 on the
+ * others.  This is the exchange step of one permanent split across GPUs.
+ * b: device descriptor as for pq_permanent_batched; partials: device,
+ * 4 * batch doubles; plan: made by pq_plan_create for the same sizes with
+ * shard_count >= 1 (required).  Allocates nothing, does not synchronise.
+ * Errors: PQ_ERR_ARG (null), PQ_ERR_STATE (plan not sharded, or made for
+ * other sizes), PQ_ERR_CUDA. */
+int pq_permanent_partials(const pq_batch* b, double* partials, pq_plan* plan, void* stream);
 
 /* Boson-sampling probabilities, Eq. (BS_prob).  U: device, m x m, U[out][in];
  * input_occ: device, m; output_occ: device, B x m; probs: device, B doubles;

@@ -28,13 +28,15 @@ def _ptr(t: torch.Tensor | None):
 
 
 def _opts(method: str, use_graph: bool, chunk_log2: int, warps_per_block: int = 0,
-          blocks_per_sm: int = 0) -> _pq.pq_plan_options:
+          blocks_per_sm: int = 0, shard: tuple[int, int] | None = None) -> _pq.pq_plan_options:
     o = _pq.pq_plan_options()
     o.method = {"batched": _pq.PQ_METHOD_BATCHED, "plain": _pq.PQ_METHOD_PLAIN}[method]
     o.use_graph = 1 if use_graph else 0
     o.chunk_log2 = int(chunk_log2)
     o.warps_per_block = int(warps_per_block)
     o.blocks_per_sm = int(blocks_per_sm)
+    if shard is not None:
+        o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
     return o
 
 
@@ -91,7 +93,9 @@ class Plan:
     @classmethod
     def for_batch(cls, pb: PermBatch | DeviceBatch, method: str = "batched",
                   use_graph: bool = False, chunk_log2: int = 0, warps_per_block: int = 0,
-                  blocks_per_sm: int = 0) -> "Plan":
+                  blocks_per_sm: int = 0, shard: tuple[int, int] | None = None) -> "Plan":
+        """Plan a ragged batch; ``shard=(index, count)`` makes a plan for one
+        shard of every permanent's warp tasks (see ``permanent_partials``)."""
         db = pb if isinstance(pb, DeviceBatch) else None
         host = db.host if db is not None else pb
         keep = [np.ascontiguousarray(x) for x in
@@ -102,17 +106,18 @@ class Plan:
         s.mat_off, s.k, s.l, s.row_mult, s.row_off, s.col_mult, s.col_off = [
             x.ctypes.data if x.size else None for x in keep]
         h = _pq.pq_plan_create(s, _opts(method, use_graph, chunk_log2, warps_per_block,
-                                        blocks_per_sm))
+                                        blocks_per_sm, shard))
         return cls(h, "batch")
 
     @classmethod
     def for_bs(cls, m: int, s, t, method: str = "batched", use_graph: bool = False,
-               chunk_log2: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0) -> "Plan":
+               chunk_log2: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0,
+               shard: tuple[int, int] | None = None) -> "Plan":
         s = np.ascontiguousarray(np.asarray(s, dtype=np.int32))
         t = np.ascontiguousarray(np.asarray(t, dtype=np.int32).reshape(-1, m))
         h = _pq.pq_plan_create_bs(int(m), s, t, int(t.shape[0]),
                                   _opts(method, use_graph, chunk_log2, warps_per_block,
-                                        blocks_per_sm))
+                                        blocks_per_sm, shard))
         return cls(h, "bs")
 
     def stats(self) -> dict:
@@ -147,6 +152,68 @@ def permanent_batched(db: DeviceBatch, plan: Plan | None = None, out: torch.Tens
     _pq.pq_permanent_batched(db.c_struct(mats), _ptr(out) if db.batch else None,
                              plan.handle if plan else None, _stream_handle(stream))
     return out
+
+
+def permanent_partials(db: DeviceBatch, plan: Plan, out: torch.Tensor | None = None,
+                       stream=None) -> torch.Tensor:
+    """This shard's unscaled double-double sums, a (batch, 4) float64 tensor
+    (re hi, re lo, im hi, im lo) on the batch's device; ``plan`` must be made
+    with ``shard=(index, count)``."""
+    if out is None:
+        out = torch.empty((db.batch, 4), dtype=torch.float64, device=db.mats.device)
+    _pq.pq_permanent_partials(db.c_struct(), _ptr(out) if db.batch else None, plan.handle,
+                              _stream_handle(stream))
+    return out
+
+
+def _two_sum(a: np.ndarray, b: np.ndarray):
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def combine_partials(parts, n) -> np.ndarray:
+    """Permanents from the shards' partial sums: the (batch, 4) arrays are
+    added in the order given with TwoSum on the high parts (double-double)
+    and scaled by 2^{-(n-1)} (n = 0: no scaling).  ``n`` holds each
+    permanent's photon number."""
+    parts = [np.asarray(p, dtype=np.float64) for p in parts]
+    rh, rl = parts[0][:, 0].copy(), parts[0][:, 1].copy()
+    ih, il = parts[0][:, 2].copy(), parts[0][:, 3].copy()
+    for p in parts[1:]:
+        rh, e = _two_sum(rh, p[:, 0])
+        rl = rl + p[:, 1] + e
+        ih, e = _two_sum(ih, p[:, 2])
+        il = il + p[:, 3] + e
+    n = np.asarray(n, dtype=np.int64)
+    shift = np.where(n > 0, 1 - n, 0)
+    return np.ldexp(rh + rl, shift) + 1j * np.ldexp(ih + il, shift)
+
+
+def gather_partials(local: torch.Tensor, group=None) -> list:
+    """Every shard's partials, in rank order, on every rank (one all_gather of
+    32 bytes per permanent: the exchange step of a split permanent).
+    Without an initialised process group this rank's partials alone."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return [local.cpu().numpy()]
+    world = dist.get_world_size(group)
+    t = local if dist.get_backend(group) == "nccl" else local.cpu()
+    bufs = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(bufs, t.contiguous(), group=group)
+    return [b.cpu().numpy() for b in bufs]
+
+
+def permanent_distributed(db: DeviceBatch, plan: Plan, group=None, stream=None) -> np.ndarray:
+    """Permanents of a batch whose Gray codes are split over the ranks of a
+    process group: each rank passes the plan of its shard (``shard=(rank,
+    world)``); returns the complex permanents on every rank."""
+    part = permanent_partials(db, plan, stream=stream)
+    torch.cuda.synchronize(db.mats.device)
+    host = db.host
+    n = np.array([int(host.row_mult[host.row_off[b]:host.row_off[b] + host.k[b]].sum())
+                  for b in range(host.batch)], dtype=np.int64)
+    return combine_partials(gather_partials(part, group), n)
 
 
 def permanent_backward(db: DeviceBatch, grad_out: torch.Tensor, plan: Plan | None = None,

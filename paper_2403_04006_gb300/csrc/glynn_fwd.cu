@@ -157,9 +157,23 @@ __device__ __forceinline__ void glynn_step(LowWalk& wk, const WarpSmem& sm, doub
         wlow = (double)low_weight(wk, J);
 }
 
-// Write per = 2^{-(n-1)} * sum, and |per|^2 * norm.
+// Write per = 2^{-(n-1)} * sum, and |per|^2 * norm; a sharded plan writes
+// its unscaled double-double sum instead.
 __device__ __forceinline__ void finalize(const ExecArgs& a, const PermDesc& D, dd2 v)
 {
+    if (a.out_partial) {
+        double* o = a.out_partial + 4 * (int64_t)D.out;
+        if (D.trivial) {
+            o[0] = 1.0;
+            o[1] = o[2] = o[3] = 0.0;
+        } else {
+            o[0] = v.rh;
+            o[1] = v.rl;
+            o[2] = v.ih;
+            o[3] = v.il;
+        }
+        return;
+    }
     double re, im;
     if (D.trivial) {
         re = 1.0;
@@ -281,7 +295,7 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
     }
     int last = 0;
     if (lane == 0) {
-        double* pp = a.partials + 4 * (int64_t)(D.slot0 + t.part);
+        double* pp = a.partials + 4 * (int64_t)(D.slot0 + t.part - D.part0);
         pp[0] = res.rh;
         pp[1] = res.rl;
         pp[2] = res.ih;

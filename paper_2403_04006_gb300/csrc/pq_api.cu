@@ -329,6 +329,10 @@ static int default_log2_for(const pq_plan* P, const ItemPlan& it)
 {
     if (P->opts.chunk_log2 > 0)
         return P->opts.chunk_log2;
+    // The shards of a permanent must cut its Gray code identically, whatever
+    // each process has tuned: sharded plans use the fixed default.
+    if (P->opts.shard_count > 0)
+        return 10;
     if (it.n >= 0 && it.n < (int)P->class_log2.size() && P->class_log2[it.n] > 0)
         return P->class_log2[it.n];
     int tuned = tune_get(it.n);
@@ -453,27 +457,38 @@ static int schedule_and_upload(pq_plan* P)
         app(it.drad);
         app(it.dtop);
         app(it.ecnt);
-        int64_t nt = it.trivial ? 1 : (it.nchunks + kWarp - 1) / kWarp;
-        if (nt > (int64_t(1) << 30))
+        const int64_t nt_all = it.trivial ? 1 : (it.nchunks + kWarp - 1) / kWarp;
+        if (nt_all > (int64_t(1) << 30))
             return fail(PQ_ERR_UNSUPPORTED, "too many tasks for one permanent");
+        // a sharded plan keeps the contiguous part range of its shard
+        int64_t q0 = 0, q1 = nt_all;
+        if (P->opts.shard_count > 1) {
+            q0 = nt_all * P->opts.shard_index / P->opts.shard_count;
+            q1 = nt_all * (P->opts.shard_index + 1) / P->opts.shard_count;
+        }
+        const int64_t nt = q1 - q0;
         D.ntasks = (int32_t)nt;
+        D.part0 = (int32_t)q0;
         D.slot0 = slot;
         slot += (int32_t)nt;
         P->plain_first[p] = (int64_t)P->tasks_plain_h.size();
         const double fpt = it.trivial ? 0.0 : fwd_flops_per_term(it);
         const double init = 2.0 * (it.drow.size() - it.J) * it.l + 2.0 * it.l;
-        for (int64_t q = 0; q < nt; ++q) {
+        for (int64_t q = q0; q < q1; ++q) {
             Task t;
             t.perm = (int32_t)p;
             t.part = (int32_t)q;
             P->tasks_plain_h.push_back(t);
             task_cost.push_back((double)it.L * fpt + init);
         }
-        if (!it.trivial) {
-            terms += it.T;
-            flops_f += (double)it.T * fpt;
-            instr_f += (double)it.T * fwd_instr_per_term(it);
-            flops_b += (double)it.T * bwd_flops_per_term(it);
+        if (!it.trivial && nt > 0) {
+            // terms of this plan's chunks (all of them unless sharded)
+            const int64_t c1 = std::min<int64_t>(it.nchunks, q1 * kWarp);
+            const int64_t tt = (c1 - q0 * kWarp) * it.L;
+            terms += tt;
+            flops_f += (double)tt * fpt;
+            instr_f += (double)tt * fwd_instr_per_term(it);
+            flops_b += (double)tt * bwd_flops_per_term(it);
             // per task, every lane: L terms, the chunk start ((ndig - J) row
             // updates of 2l), the chunk's fold and scaling (28) and the lane
             // tree (92); per permanent with several tasks, the partials'
@@ -563,6 +578,10 @@ static int plan_common_init(pq_plan* P, const pq_plan_options* opts)
         return fail(PQ_ERR_ARG, "warps_per_block %d outside [0, 16]", P->opts.warps_per_block);
     if (P->opts.blocks_per_sm < 0 || P->opts.blocks_per_sm > 32)
         return fail(PQ_ERR_ARG, "blocks_per_sm %d outside [0, 32]", P->opts.blocks_per_sm);
+    if (P->opts.shard_count < 0 || P->opts.shard_count > 65536 || P->opts.shard_index < 0 ||
+        (P->opts.shard_count > 0 && P->opts.shard_index >= P->opts.shard_count) ||
+        (P->opts.shard_count == 0 && P->opts.shard_index != 0))
+        return fail(PQ_ERR_ARG, "shard %d of %d", P->opts.shard_index, P->opts.shard_count);
     PQ_CUDA(cudaGetDevice(&P->device));
     PQ_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
     return PQ_OK;
@@ -652,6 +671,8 @@ extern "C" int pq_plan_create_bs(int32_t m, const int32_t* in_occ, const int32_t
         ns += in_occ[i];
         fs *= factorial_d(in_occ[i]);
     }
+    if (opts && opts->shard_count > 1)
+        return fail(PQ_ERR_UNSUPPORTED, "boson-sampling plans are not sharded");
     pq_plan* P = new (std::nothrow) pq_plan();
     if (!P)
         return fail(PQ_ERR_NOMEM, "host allocation failed");
@@ -721,9 +742,11 @@ extern "C" int pq_plan_get_stats(const pq_plan* P, pq_plan_stats* out)
 }
 
 // ---------------------------------------------------------------- execution
-static ExecArgs exec_args(pq_plan* P, const void* src, void* amps, double* probs, bool batched)
+static ExecArgs exec_args(pq_plan* P, const void* src, void* amps, double* probs, bool batched,
+                          double* partial = nullptr)
 {
     ExecArgs a;
+    a.out_partial = partial;
     a.desc = P->desc_d;
     a.meta = P->meta_d;
     a.tasks = batched ? P->tasks_batched_d : P->tasks_plain_d;
@@ -738,13 +761,13 @@ static ExecArgs exec_args(pq_plan* P, const void* src, void* amps, double* probs
 }
 
 static int run_forward_raw(pq_plan* P, const void* src, void* amps, double* probs,
-                           cudaStream_t st)
+                           cudaStream_t st, double* partial = nullptr)
 {
     PQ_CUDA(cudaMemsetAsync(P->counters_d, 0, (size_t)(P->nperm + 1) * sizeof(int32_t), st));
     if (P->nperm == 0)
         return PQ_OK;
     if (P->opts.method == PQ_METHOD_PLAIN) {
-        ExecArgs a = exec_args(P, src, amps, probs, false);
+        ExecArgs a = exec_args(P, src, amps, probs, false, partial);
         for (int64_t p = 0; p < P->nperm; ++p) {
             cudaError_t e = fwd_launch_plain(P->lmax, a, P->plain_first[p], P->plain_first[p + 1],
                                              P->kmax, P->wpb, st);
@@ -753,7 +776,7 @@ static int run_forward_raw(pq_plan* P, const void* src, void* amps, double* prob
         }
         return PQ_OK;
     }
-    ExecArgs a = exec_args(P, src, amps, probs, true);
+    ExecArgs a = exec_args(P, src, amps, probs, true, partial);
     cudaError_t e = fwd_launch_persistent(P->lmax, a, P->kmax, P->blocks, P->wpb, st);
     if (e != cudaSuccess)
         return fail(PQ_ERR_CUDA, "persistent launch failed: %s", cudaGetErrorString(e));
@@ -854,10 +877,13 @@ static int fetch_sizes(const pq_batch* b, HostSizes& h)
     return PQ_OK;
 }
 
-static int check_batch_plan(const pq_plan* P, const pq_batch* b)
+static int check_batch_plan(const pq_plan* P, const pq_batch* b, bool sharded = false)
 {
     if (P->kind != 0)
         return fail(PQ_ERR_STATE, "plan was made for boson sampling, not a permanent batch");
+    if (sharded != (P->opts.shard_count > 0))
+        return fail(PQ_ERR_STATE, sharded ? "plan is not sharded: use pq_permanent_batched"
+                                          : "sharded plan: use pq_permanent_partials");
     if (b->batch != P->nperm)
         return fail(PQ_ERR_STATE, "plan made for %lld items, batch has %lld",
                     (long long)P->nperm, (long long)b->batch);
@@ -894,6 +920,22 @@ extern "C" int pq_permanent_batched(const pq_batch* b, pq_c128* out, pq_plan* pl
     }
     pq_plan_destroy(P);
     return rc;
+}
+
+extern "C" int pq_permanent_partials(const pq_batch* b, double* partials, pq_plan* plan,
+                                     void* stream)
+{
+    if (!b || !plan || (b->batch > 0 && (!partials || !b->mats)))
+        return fail(PQ_ERR_ARG, "null argument");
+    int rc = check_batch_plan(plan, b, true);
+    if (rc != PQ_OK)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->batch == 0)
+        return PQ_OK;
+    // permanents none of whose tasks fall in this shard contribute zero
+    PQ_CUDA(cudaMemsetAsync(partials, 0, (size_t)b->batch * 4 * sizeof(double), st));
+    return run_forward_raw(plan, b->mats, nullptr, nullptr, st, partials);
 }
 
 extern "C" int pq_bs_probs(const pq_c128* U, int32_t m, const int32_t* in_occ,
@@ -1147,6 +1189,8 @@ static int ensure_backward(pq_plan* P)
 static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, const double* grad_prob,
                         const pq_c128* amps, cudaStream_t st)
 {
+    if (P->opts.shard_count > 0)
+        return fail(PQ_ERR_UNSUPPORTED, "the backward does not run on a sharded plan");
     int rc = ensure_backward(P);
     if (rc != PQ_OK)
         return rc;
@@ -1318,6 +1362,8 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
 {
     if (!P)
         return fail(PQ_ERR_ARG, "null plan");
+    if (P->opts.shard_count > 0)
+        return fail(PQ_ERR_STATE, "a sharded plan keeps the fixed chunking all shards share");
     const void* src = nullptr;
     if (P->kind == 0) {
         if (!b)

@@ -49,7 +49,8 @@ struct alignas(16) PermDesc {
     int32_t jf;       // first product column whose prefix is an extra factor (-1: none)
     int64_t L;        // chunk length
     double norm;      // 1 / (prod t! prod s!) for boson sampling, else 1
-    double pad2;
+    int32_t part0;    // first task part of this plan's shard (0 unless sharded)
+    int32_t pad2;
 };
 
 // Integer metadata of one permanent, at pool + PermDesc::meta:
@@ -69,7 +70,8 @@ inline int meta_size(int k, int l, int ndig) { return 2 * k + 3 * l + 3 * ndig; 
 struct alignas(8) Task {
     int32_t perm;  // permanent
     int32_t part;  // index of this task among its permanent's tasks; it covers
-                   // chunks [32 part, min(32 part + 32, nchunks))
+                   // chunks [32 part, min(32 part + 32, nchunks)); a sharded
+                   // plan holds the parts [part0, part0 + ntasks) of each
 };
 
 // Arguments of one kernel execution (device pointers).
@@ -81,6 +83,8 @@ struct ExecArgs {
     const double2* src;   // matrices (batch) or U (boson sampling)
     double2* out_amp;     // permanents, nullable
     double* out_prob;     // |per|^2 * norm, nullable
+    double* out_partial;  // sharded plans: unscaled double-double sum, 4 doubles per
+                          // permanent (re hi, re lo, im hi, im lo); nullable
     double* partials;     // 4 doubles per task slot
     int32_t* counters;    // [0] task queue head, [1 + p] finished tasks of p
     int32_t* err;         // device error word (0 = ok)

@@ -291,6 +291,7 @@ extern "C" int pq_permanent_noalloc(const pq_c128* B, int32_t k, int32_t l,
     a.src = reinterpret_cast<const double2*>(B);
     a.out_amp = reinterpret_cast<double2*>(out);
     a.out_prob = nullptr;
+    a.out_partial = nullptr;
     a.partials = partials_d;
     a.counters = counters_d;
     a.err = counters_d + 8;

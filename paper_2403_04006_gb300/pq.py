@@ -44,7 +44,8 @@ class pq_batch_sizes(ctypes.Structure):
 
 class pq_plan_options(ctypes.Structure):
     _fields_ = [("method", _i32), ("use_graph", _i32), ("chunk_log2", _i32),
-                ("warps_per_block", _i32), ("blocks_per_sm", _i32), ("reserved", _i32 * 3)]
+                ("warps_per_block", _i32), ("blocks_per_sm", _i32), ("shard_index", _i32),
+                ("shard_count", _i32), ("reserved", _i32)]
 
 
 class pq_plan_stats(ctypes.Structure):
@@ -64,6 +65,7 @@ _SIGNATURES = {
                                  ctypes.POINTER(_vp)]),
     "pq_plan_destroy": (_i32, [_vp]),
     "pq_permanent_batched": (_i32, [ctypes.POINTER(pq_batch), _vp, _vp, _vp]),
+    "pq_permanent_partials": (_i32, [ctypes.POINTER(pq_batch), _vp, _vp, _vp]),
     "pq_bs_probs": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "pq_permanent_backward": (_i32, [ctypes.POINTER(pq_batch), _vp, _vp, _vp, _vp]),
     "pq_bs_probs_backward": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
@@ -147,6 +149,11 @@ def pq_plan_destroy(plan: int):
 def pq_permanent_batched(b: pq_batch, out_ptr: int, plan: int | None, stream: int | None):
     _check(load_library().pq_permanent_batched(ctypes.byref(b), out_ptr, plan, stream),
            "pq_permanent_batched")
+
+
+def pq_permanent_partials(b: pq_batch, partials_ptr: int, plan: int, stream: int | None):
+    _check(load_library().pq_permanent_partials(ctypes.byref(b), partials_ptr, plan, stream),
+           "pq_permanent_partials")
 
 
 def pq_bs_probs(U_ptr, m, in_ptr, out_ptr, B, probs_ptr, amps_ptr, plan, stream):

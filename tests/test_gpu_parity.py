@@ -461,3 +461,48 @@ def test_plans_run_inside_a_callers_graph_capture(dev, use_graph):
             Bn = new[o:o + B.size].reshape(B.shape)
             ref = O.perm_ryser(Bn, r, c, gold=True)
             assert abs(ref_out[b] - ref) <= TOL * max(abs(ref), 1e-300)
+
+
+@pytest.mark.parametrize("nshards", [1, 2, 3, 7])
+def test_sharded_plans_sum_to_the_permanents(dev, nshards):
+    """Every shard's plan covers its range of each permanent's warp tasks; the
+    shards' partials, combined in double-double, give the permanents.  The
+    shards run one after another on this GPU (no shard waits on another)."""
+    rng = np.random.default_rng(808)
+    A = W.single_large(30)[:20, :20]
+    items = [(A, [1] * 20, [1] * 20)]                 # 2^19 terms: many tasks
+    items += random_items(10, 2, 12, rng)             # fewer tasks than shards
+    items.append((np.zeros((0, 0)), [], []))          # n = 0
+    pb = W.pack_batch(items)
+    db = api.DeviceBatch(pb, dev)
+    ref = api.permanent_batched(db, api.Plan.for_batch(pb)).cpu().numpy()
+    parts = []
+    for r in range(nshards):
+        plan = api.Plan.for_batch(pb, shard=(r, nshards))
+        parts.append(api.permanent_partials(db, plan).cpu().numpy())
+    n = np.array([int(np.sum(r)) for _, r, _ in items])
+    got = api.combine_partials(parts, n)
+    assert got[-1] == 1.0
+    for b, (B, r, c) in enumerate(items[:-1]):
+        assert abs(got[b] - ref[b]) <= 1e-13 * abs(ref[b])
+    w0 = O.perm_ryser(A, gold=True)
+    assert abs(got[0] - w0) <= TOL * abs(w0)
+
+
+def test_sharded_plan_misuse(dev):
+    pb = W.pack_batch([(np.eye(3) + 0j, [1, 1, 1], [1, 1, 1])])
+    db = api.DeviceBatch(pb, dev)
+    sh = api.Plan.for_batch(pb, shard=(0, 2))
+    plain = api.Plan.for_batch(pb)
+    for call, code in ((lambda: api.permanent_batched(db, sh), pq.PQ_ERR_STATE),
+                       (lambda: api.permanent_partials(db, plain), pq.PQ_ERR_STATE),
+                       (lambda: sh.autotune(db), pq.PQ_ERR_STATE),
+                       (lambda: api.permanent_backward(
+                           db, torch.ones(1, dtype=torch.complex128, device=dev), sh),
+                        pq.PQ_ERR_STATE),
+                       (lambda: api.Plan.for_batch(pb, shard=(2, 2)), pq.PQ_ERR_ARG),
+                       (lambda: api.Plan.for_bs(3, [1, 1, 1], [[1, 1, 1]], shard=(0, 2)),
+                        pq.PQ_ERR_UNSUPPORTED)):
+        with pytest.raises(pq.PQError) as e:
+            call()
+        assert e.value.code == code
