@@ -408,15 +408,21 @@ static int schedule_and_upload(pq_plan* P)
     P->lmax = lmax_needed;
     P->kmax = kmax;
     // The plain method runs one permanent per launch, so each permanent is cut
-    // finely enough to occupy the whole GPU (about 4 warps per SM); the batched
-    // method keeps a warp's worth of chunks per permanent and fills the GPU
-    // with many permanents at once.
-    const int64_t plain_chunks = (int64_t)P->num_sms * 4 * kWarp;
-    for (ItemPlan& it : P->items)
+    // finely enough to occupy the whole GPU: at least 4 warps per SM, and for
+    // a large permanent up to two waves of 16 resident warps per SM (chunks of
+    // at least 64 terms, so that each chunk's start stays cheap; eight waves
+    // measured slower at 2.9e7 terms).
+    // The batched method keeps a warp's worth of chunks per permanent and
+    // fills the GPU with many permanents at once.
+    const int64_t plain_min = (int64_t)P->num_sms * 4 * kWarp;
+    const int64_t plain_max = (int64_t)P->num_sms * 16 * 2 * kWarp;
+    for (ItemPlan& it : P->items) {
+        const int64_t plain_chunks = std::max(plain_min, std::min(plain_max, it.T / 64));
         choose_chunks(it, default_log2_for(P, it), kMaxLowDigits,
                       (P->opts.method == PQ_METHOD_PLAIN && P->opts.chunk_log2 == 0)
                           ? plain_chunks
                           : kWarp);
+    }
 
     P->desc_h.assign(np, PermDesc{});
     P->meta_h.clear();
