@@ -1033,8 +1033,11 @@ static int ensure_backward(pq_plan* P)
     // Low digits per chunk for each class: each digit costs every lane one row
     // of corrections; fewer digits mean shorter chunks whose start-up (column
     // sums from the high digits, about 2l(n - J) operations) is paid more
-    // often.  Take the J that maximises (share of the four warps per SM that
-    // saturate the FP64 pipe) x (share of the work that is per-term work).
+    // often.  Take the J that maximises (share of 8 warps per SM) x (share of
+    // the work that is per-term work): four warps saturate a plain FP64 loop,
+    // but the backward's prefix and suffix chains wait on their own results,
+    // and a second warp per SMSP hides that (ragged batch: 121 ms with the
+    // share taken of 4 warps, 114 ms of 6 or 8).
     for (int c = 0; c < ncls; ++c) {
         if (!cls_used[c])
             continue;
@@ -1047,7 +1050,7 @@ static int ensure_backward(pq_plan* P)
                 continue;
             int wpb = 0, bps = 0;
             launch_geometry_max(bwd_regs_per_thread(C.ld), per_warp, 8, wpb, bps);
-            const double warps = std::min(4.0, (double)(wpb * bps)) / 4.0;
+            const double warps = std::min(8.0, (double)(wpb * bps)) / 8.0;
             const double per_term = 18.0 * C.ld + 8.0;
             const double start = std::max(0.0, nbar - J) * 2.0 * C.ld / (double)(1 << J);
             const double score = warps * per_term / (per_term + start);
