@@ -475,7 +475,8 @@ def extra_measurements(args, dev, stream, flush, peak_tflops, fp64_lane_ops):
     res["paper_repeated_2x"] = sweep
     # the paper's repeated hafnian / loop hafnian benchmark shape (Figs.
     # hafnian, loop_hafnian): k x k GBS matrix, every index repeated twice
-    # (N = 2k); one synchronous call each (planning and upload included)
+    # (N = 2k); one synchronous call each (planning and upload included), and
+    # the launch of a plan made once
     for loop in (False, True):
         hs = {}
         for k in range(4, 21, 2):
@@ -485,7 +486,13 @@ def extra_measurements(args, dev, stream, flush, peak_tflops, fp64_lane_ops):
             terms = 2 * 3 ** (k - 1)
             ms = timed(lambda: api.hafnian_repeated(Bd, [0], [k], r, [0], gamma=gd,
                                                     stream=stream), 3)
-            hs[str(k)] = {"N": 2 * k, "ms": ms, "terms": terms, "terms_per_s": terms / ms * 1e3}
+            # the same through a plan made once: the launch alone
+            hplan = api.HafnianPlan([0], [k], r, [0], loop=loop)
+            hout = torch.empty(1, dtype=torch.complex128, device=dev)
+            ms_p = timed(lambda: hplan.run(Bd, gamma=gd, out=hout, stream=stream), 3)
+            hplan.close()
+            hs[str(k)] = {"N": 2 * k, "ms": ms, "terms": terms, "terms_per_s": terms / ms * 1e3,
+                          "ms_planned": ms_p, "terms_per_s_planned": terms / ms_p * 1e3}
         res["paper_loop_hafnian_2x" if loop else "paper_hafnian_2x"] = hs
     # Algorithm A sampler (one batched launch per photon over all samples),
     # m = 16 Haar interferometer, 8 photons, 2000 samples

@@ -264,6 +264,25 @@ int pq_hafnian_repeated(const pq_c128* mats, const int64_t* mat_off, const int32
                         const int32_t* rep, const int64_t* rep_off, int64_t batch, pq_c128* out,
                         void* stream);
 
+/* Planned (loop) hafnians, for callers that evaluate the same shapes many
+ * times: pq_hafnian_plan_create does the host planning of pq_hafnian_repeated
+ * (loop = 0) or pq_loop_hafnian_repeated (loop = 1) once for the sizes and
+ * repetitions given (host arrays, copied; same layout and limits as those
+ * calls), uploads the schedule and allocates the device workspace.
+ * pq_hafnian_plan_run then evaluates the batch for the matrix values at mats
+ * (and loop weights at gamma when loop = 1; device, same layout as those
+ * calls) into out (device, batch complex): it allocates nothing, reads no
+ * host memory and does not synchronise `stream`.  One plan serves one stream
+ * at a time.  pq_hafnian_plan_destroy synchronises the device and frees the
+ * plan.  Errors as for pq_hafnian_repeated; PQ_ERR_ARG for a null plan, or a
+ * null gamma on a loop plan. */
+typedef struct pq_haf_plan pq_haf_plan;
+int pq_hafnian_plan_create(const int64_t* mat_off, const int32_t* k, const int32_t* rep,
+                           const int64_t* rep_off, int64_t batch, int32_t loop, pq_haf_plan** out);
+int pq_hafnian_plan_run(pq_haf_plan* plan, const pq_c128* mats, const pq_c128* gamma, pq_c128* out,
+                        void* stream);
+int pq_hafnian_plan_destroy(pq_haf_plan* plan);
+
 /* Loop hafnians with repeated indices (Eq. (loop_hafnian), with the filldiag
  * of the displaced Gaussian detection probability in Appendix A: every copy
  * of base index i gets the loop weight gamma_i on the diagonal).  Item b is

@@ -363,3 +363,37 @@ def hafnian_repeated(mats: torch.Tensor, mat_off, k, rep, rep_off, gamma: torch.
                             np.asarray(rep_off), _ptr(out) if nb else None,
                             _stream_handle(stream), gamma_ptr=_ptr(gc), loop=gc is not None)
     return out
+
+
+class HafnianPlan:
+    """A planned batch of hafnians (or loop hafnians with ``loop=True``) of
+    fixed sizes and repetitions (pq_hafnian_plan_*): ``run`` evaluates it for
+    new matrix values (and loop weights) without planning, allocating in the
+    library or synchronising."""
+
+    def __init__(self, mat_off, k, rep, rep_off, loop: bool = False):
+        self.batch = len(k)
+        self.loop = bool(loop)
+        self.handle = _pq.pq_hafnian_plan_create(np.asarray(mat_off), np.asarray(k),
+                                                 np.asarray(rep), np.asarray(rep_off), loop)
+
+    def run(self, mats: torch.Tensor, gamma: torch.Tensor | None = None,
+            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.batch, dtype=torch.complex128, device=mats.device)
+        mc = mats.contiguous()
+        gc = None if gamma is None else gamma.contiguous()
+        _pq.pq_hafnian_plan_run(self.handle, _ptr(mc), _ptr(gc), _ptr(out) if self.batch else None,
+                                _stream_handle(stream))
+        return out
+
+    def close(self):
+        if self.handle:
+            _pq.pq_hafnian_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

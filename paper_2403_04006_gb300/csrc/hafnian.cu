@@ -525,12 +525,44 @@ static double factorial_h(int n)
 }
 
 // Plan, upload, run and synchronise; gamma == nullptr selects the hafnian.
-static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32_t* k,
-                        const int32_t* rep, const int64_t* rep_off, const pq_c128* gamma,
-                        int64_t batch, pq_c128* out, void* stream)
+}  // namespace pqi
+
+// A planned batch of (loop) hafnians: host schedule uploaded once, device
+// workspace owned by the plan.
+struct pq_haf_plan {
+    int loop = 0;
+    int64_t batch = 0, ntasks = 0;
+    int kmax = 1, jmax = 1, wpb = 1, blocks = 1, per_warp = 0;
+    pqi::HafDesc* desc_d = nullptr;
+    int32_t* meta_d = nullptr;
+    pqi::Task* tasks_d = nullptr;
+    double* part_d = nullptr;
+    int32_t* cnt_d = nullptr;
+    double* loopc_d = nullptr;
+};
+
+namespace pqi {
+
+static void haf_plan_free(pq_haf_plan* P)
 {
-    const bool loop = gamma != nullptr;
-    if (batch < 0 || (batch > 0 && (!mats || !mat_off || !k || !rep || !rep_off || !out)))
+    if (!P)
+        return;
+    cudaFree(P->desc_d);
+    cudaFree(P->meta_d);
+    cudaFree(P->tasks_d);
+    cudaFree(P->part_d);
+    cudaFree(P->cnt_d);
+    cudaFree(P->loopc_d);
+    delete P;
+}
+
+// Plan: digits, chunks, tasks (longest first), loop-polynomial factors;
+// uploads them and raises the kernel's shared-memory limit.
+static int haf_plan_build(const int64_t* mat_off, const int32_t* k, const int32_t* rep,
+                          const int64_t* rep_off, int64_t batch, bool loop, pq_haf_plan** out)
+{
+    *out = nullptr;
+    if (batch < 0 || (batch > 0 && (!mat_off || !k || !rep || !rep_off)))
         return report(PQ_ERR_ARG, "null argument or negative batch");
     if (batch > (int64_t(1) << 30))
         return report(PQ_ERR_UNSUPPORTED, "batch above 2^30");
@@ -689,8 +721,15 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
         }
         slot += (int32_t)nt;
     }
-    if (batch == 0)
+    pq_haf_plan* P = new (std::nothrow) pq_haf_plan();
+    if (!P)
+        return report(PQ_ERR_NOMEM, "host allocation failed");
+    P->loop = loop ? 1 : 0;
+    P->batch = batch;
+    if (batch == 0) {
+        *out = P;
         return PQ_OK;
+    }
     // longest task first
     std::vector<int64_t> order(tasks.size());
     std::iota(order.begin(), order.end(), 0);
@@ -699,75 +738,105 @@ static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32
     std::vector<Task> sorted(tasks.size());
     for (size_t q = 0; q < order.size(); ++q)
         sorted[q] = tasks[order[q]];
-    cudaStream_t st = (cudaStream_t)stream;
-    HafDesc* desc_d = nullptr;
-    int32_t* meta_d = nullptr;
-    Task* tasks_d = nullptr;
-    double* part_d = nullptr;
-    int32_t* cnt_d = nullptr;
-    double* loopc_d = nullptr;
+    P->ntasks = (int64_t)sorted.size();
+    P->kmax = kmax;
+    P->jmax = jmax;
     int rc = PQ_OK;
-    if (cudaMalloc((void**)&loopc_d, sizeof(double) * std::max<size_t>(loopc.size(), 1)) != cudaSuccess ||
-        cudaMalloc((void**)&desc_d, sizeof(HafDesc) * batch) != cudaSuccess ||
-        cudaMalloc((void**)&meta_d, sizeof(int32_t) * std::max<size_t>(meta.size(), 1)) != cudaSuccess ||
-        cudaMalloc((void**)&tasks_d, sizeof(Task) * sorted.size()) != cudaSuccess ||
-        cudaMalloc((void**)&part_d, sizeof(double) * 4 * std::max<int32_t>(slot, 1)) != cudaSuccess ||
-        cudaMalloc((void**)&cnt_d, sizeof(int32_t) * (batch + 1)) != cudaSuccess)
+    if (cudaMalloc((void**)&P->loopc_d, sizeof(double) * std::max<size_t>(loopc.size(), 1)) !=
+            cudaSuccess ||
+        cudaMalloc((void**)&P->desc_d, sizeof(HafDesc) * batch) != cudaSuccess ||
+        cudaMalloc((void**)&P->meta_d, sizeof(int32_t) * std::max<size_t>(meta.size(), 1)) !=
+            cudaSuccess ||
+        cudaMalloc((void**)&P->tasks_d, sizeof(Task) * sorted.size()) != cudaSuccess ||
+        cudaMalloc((void**)&P->part_d, sizeof(double) * 4 * std::max<int32_t>(slot, 1)) !=
+            cudaSuccess ||
+        cudaMalloc((void**)&P->cnt_d, sizeof(int32_t) * (batch + 1)) != cudaSuccess)
         rc = report(PQ_ERR_NOMEM, "hafnian workspace allocation failed");
     if (rc == PQ_OK &&
-        (cudaMemcpyAsync(desc_d, desc.data(), sizeof(HafDesc) * batch, cudaMemcpyHostToDevice,
-                         st) != cudaSuccess ||
-         (!meta.empty() && cudaMemcpyAsync(meta_d, meta.data(), sizeof(int32_t) * meta.size(),
-                                           cudaMemcpyHostToDevice, st) != cudaSuccess) ||
-         cudaMemcpyAsync(tasks_d, sorted.data(), sizeof(Task) * sorted.size(),
-                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
-         (!loopc.empty() && cudaMemcpyAsync(loopc_d, loopc.data(), sizeof(double) * loopc.size(),
-                                            cudaMemcpyHostToDevice, st) != cudaSuccess) ||
-         cudaMemsetAsync(cnt_d, 0, sizeof(int32_t) * (batch + 1), st) != cudaSuccess))
+        (cudaMemcpy(P->desc_d, desc.data(), sizeof(HafDesc) * batch, cudaMemcpyHostToDevice) !=
+             cudaSuccess ||
+         (!meta.empty() && cudaMemcpy(P->meta_d, meta.data(), sizeof(int32_t) * meta.size(),
+                                      cudaMemcpyHostToDevice) != cudaSuccess) ||
+         cudaMemcpy(P->tasks_d, sorted.data(), sizeof(Task) * sorted.size(),
+                    cudaMemcpyHostToDevice) != cudaSuccess ||
+         (!loopc.empty() && cudaMemcpy(P->loopc_d, loopc.data(), sizeof(double) * loopc.size(),
+                                       cudaMemcpyHostToDevice) != cudaSuccess)))
         rc = report(PQ_ERR_CUDA, "hafnian upload failed");
     if (rc == PQ_OK) {
-        const int per_warp = haf_warp_smem_bytes(kmax, jmax);
+        P->per_warp = haf_warp_smem_bytes(kmax, jmax);
         int wpb = 8;
-        while (wpb > 1 && wpb * per_warp > 227 * 1024)
+        while (wpb > 1 && wpb * P->per_warp > 227 * 1024)
             --wpb;
-        const int bps = std::max(1, std::min(2, (227 * 1024) / (wpb * per_warp)));
-        HafArgs a;
-        a.desc = desc_d;
-        a.meta = meta_d;
-        a.tasks = tasks_d;
-        a.ntasks = (int64_t)sorted.size();
-        a.src = reinterpret_cast<const double2*>(mats);
-        a.gamma = reinterpret_cast<const double2*>(gamma);
-        a.loopc = loopc_d;
-        a.out = reinterpret_cast<double2*>(out);
-        a.partials = part_d;
-        a.counters = cnt_d;
-        const int64_t want_blocks = (a.ntasks + wpb - 1) / wpb;
-        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * bps, want_blocks));
-        cudaError_t e;
-        if (loop) {
-            e = cudaFuncSetAttribute(hafnian_kernel<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * per_warp);
-            if (e == cudaSuccess)
-                hafnian_kernel<true><<<blocks, 32 * wpb, wpb * per_warp, st>>>(a, kmax, jmax);
-        } else {
-            e = cudaFuncSetAttribute(hafnian_kernel<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * per_warp);
-            if (e == cudaSuccess)
-                hafnian_kernel<false><<<blocks, 32 * wpb, wpb * per_warp, st>>>(a, kmax, jmax);
-        }
-        if (e != cudaSuccess || cudaGetLastError() != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            rc = report(PQ_ERR_CUDA, "hafnian kernel failed");
-    } else {
-        cudaStreamSynchronize(st);
+        const int bps = std::max(1, std::min(2, (227 * 1024) / (wpb * P->per_warp)));
+        P->wpb = wpb;
+        const int64_t want_blocks = (P->ntasks + wpb - 1) / wpb;
+        P->blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * bps, want_blocks));
+        // raise (never lower) the dynamic shared-memory limit of the kernel
+        cudaFuncAttributes at{};
+        cudaError_t e = loop ? cudaFuncGetAttributes(&at, hafnian_kernel<true>)
+                             : cudaFuncGetAttributes(&at, hafnian_kernel<false>);
+        const int need = wpb * P->per_warp;
+        if (e == cudaSuccess && at.maxDynamicSharedSizeBytes < need)
+            e = loop ? cudaFuncSetAttribute(hafnian_kernel<true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, need)
+                     : cudaFuncSetAttribute(hafnian_kernel<false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        if (e != cudaSuccess)
+            rc = report(PQ_ERR_CUDA, "hafnian kernel attribute setup failed");
     }
-    cudaFree(desc_d);
-    cudaFree(meta_d);
-    cudaFree(tasks_d);
-    cudaFree(part_d);
-    cudaFree(cnt_d);
-    cudaFree(loopc_d);
+    if (rc != PQ_OK) {
+        haf_plan_free(P);
+        return rc;
+    }
+    *out = P;
+    return PQ_OK;
+}
+
+// Execution: clear the counters and launch; allocates nothing, no sync.
+static int haf_plan_launch(pq_haf_plan* P, const pq_c128* mats, const pq_c128* gamma,
+                           pq_c128* out, cudaStream_t st)
+{
+    if (P->batch == 0)
+        return PQ_OK;
+    if (cudaMemsetAsync(P->cnt_d, 0, sizeof(int32_t) * (P->batch + 1), st) != cudaSuccess)
+        return report(PQ_ERR_CUDA, "hafnian counter reset failed");
+    HafArgs a;
+    a.desc = P->desc_d;
+    a.meta = P->meta_d;
+    a.tasks = P->tasks_d;
+    a.ntasks = P->ntasks;
+    a.src = reinterpret_cast<const double2*>(mats);
+    a.gamma = reinterpret_cast<const double2*>(gamma);
+    a.loopc = P->loopc_d;
+    a.out = reinterpret_cast<double2*>(out);
+    a.partials = P->part_d;
+    a.counters = P->cnt_d;
+    const int smem = P->wpb * P->per_warp;
+    if (P->loop)
+        hafnian_kernel<true><<<P->blocks, 32 * P->wpb, smem, st>>>(a, P->kmax, P->jmax);
+    else
+        hafnian_kernel<false><<<P->blocks, 32 * P->wpb, smem, st>>>(a, P->kmax, P->jmax);
+    if (cudaGetLastError() != cudaSuccess)
+        return report(PQ_ERR_CUDA, "hafnian kernel launch failed");
+    return PQ_OK;
+}
+
+// The one-shot calls: plan, run, synchronise, free.
+static int run_hafnians(const pq_c128* mats, const int64_t* mat_off, const int32_t* k,
+                        const int32_t* rep, const int64_t* rep_off, const pq_c128* gamma,
+                        int64_t batch, pq_c128* out, void* stream)
+{
+    if (batch > 0 && (!mats || !out))
+        return report(PQ_ERR_ARG, "null argument");
+    pq_haf_plan* P = nullptr;
+    int rc = haf_plan_build(mat_off, k, rep, rep_off, batch, gamma != nullptr, &P);
+    if (rc != PQ_OK)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = haf_plan_launch(P, mats, gamma, out, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == PQ_OK)
+        rc = report(PQ_ERR_CUDA, "hafnian kernel failed");
+    haf_plan_free(P);
     return rc;
 }
 
@@ -797,5 +866,34 @@ extern "C" int pq_loop_poly_factors(int32_t N, double* out)
     const std::vector<double> cf = pqi::loop_factors(N);
     for (size_t i = 0; i < cf.size(); ++i)
         out[i] = cf[i];
+    return PQ_OK;
+}
+
+extern "C" int pq_hafnian_plan_create(const int64_t* mat_off, const int32_t* k, const int32_t* rep,
+                                      const int64_t* rep_off, int64_t batch, int32_t loop,
+                                      pq_haf_plan** out)
+{
+    if (!out)
+        return pqi::report(PQ_ERR_ARG, "null output");
+    return pqi::haf_plan_build(mat_off, k, rep, rep_off, batch, loop != 0, out);
+}
+
+extern "C" int pq_hafnian_plan_run(pq_haf_plan* plan, const pq_c128* mats, const pq_c128* gamma,
+                                   pq_c128* out, void* stream)
+{
+    if (!plan)
+        return pqi::report(PQ_ERR_ARG, "null plan");
+    if (plan->batch > 0 && (!mats || !out || (plan->loop && !gamma)))
+        return pqi::report(PQ_ERR_ARG, "null argument");
+    return pqi::haf_plan_launch(plan, mats, plan->loop ? gamma : nullptr, out,
+                                (cudaStream_t)stream);
+}
+
+extern "C" int pq_hafnian_plan_destroy(pq_haf_plan* plan)
+{
+    if (plan) {
+        cudaDeviceSynchronize();
+        pqi::haf_plan_free(plan);
+    }
     return PQ_OK;
 }

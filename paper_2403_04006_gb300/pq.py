@@ -80,6 +80,9 @@ _SIGNATURES = {
     "pq_bs_probs_lossy": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp]),
     "pq_hafnian_repeated": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "pq_loop_hafnian_repeated": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "pq_hafnian_plan_create": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, ctypes.POINTER(_vp)]),
+    "pq_hafnian_plan_run": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "pq_hafnian_plan_destroy": (_i32, [_vp]),
     "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "pq_loop_poly_factors": (_i32, [_i32, _vp]),
@@ -250,6 +253,31 @@ def pq_hafnian_repeated(mats_ptr, mat_off: np.ndarray, k: np.ndarray, rep: np.nd
                "pq_loop_hafnian_repeated")
     else:
         _check(lib.pq_hafnian_repeated(mats_ptr, *args), "pq_hafnian_repeated")
+
+
+def pq_hafnian_plan_create(mat_off, k, rep, rep_off, loop: bool) -> int:
+    """Plan a (loop) hafnian batch from host sizes and repetitions; returns the handle."""
+    mo = np.ascontiguousarray(mat_off, dtype=np.int64)
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    r = np.ascontiguousarray(rep, dtype=np.int32)
+    ro = np.ascontiguousarray(rep_off, dtype=np.int64)
+    nb = kk.shape[0]
+    h = _vp()
+    _check(load_library().pq_hafnian_plan_create(
+        mo.ctypes.data if nb else None, kk.ctypes.data if nb else None,
+        r.ctypes.data if r.size else (kk.ctypes.data if nb else None),
+        ro.ctypes.data if nb else None, nb, 1 if loop else 0, ctypes.byref(h)),
+        "pq_hafnian_plan_create")
+    return h.value
+
+
+def pq_hafnian_plan_run(plan: int, mats_ptr, gamma_ptr, out_ptr, stream):
+    _check(load_library().pq_hafnian_plan_run(plan, mats_ptr, gamma_ptr, out_ptr, stream),
+           "pq_hafnian_plan_run")
+
+
+def pq_hafnian_plan_destroy(plan: int):
+    _check(load_library().pq_hafnian_plan_destroy(plan), "pq_hafnian_plan_destroy")
 
 
 def pq_loop_poly_factors(N: int) -> np.ndarray:

@@ -179,3 +179,38 @@ def test_errors(dev):
                                gamma_ptr=None, loop=True)
     assert e.value.code == pq.PQ_ERR_ARG
     assert api.hafnian_repeated(B, [], [], [], []).numel() == 0
+
+
+@pytest.mark.parametrize("loop", [False, True])
+def test_plan_runs_match_the_one_shot_call(dev, loop):
+    """A hafnian plan evaluates the same values as the one-shot call, run
+    after run, for new matrix values each time."""
+    mats, mo, k, rep, ro, gam = W.hafnian_batch(120, kmin=1, kmax=7, rmax=3, seed_stream=11)
+    plan = api.HafnianPlan(mo, k, rep, ro, loop=loop)
+    rng = np.random.default_rng(12)
+    for _ in range(3):
+        m = (rng.standard_normal(mats.shape) + 1j * rng.standard_normal(mats.shape)) * 0.4
+        g = (rng.standard_normal(gam.shape) + 1j * rng.standard_normal(gam.shape)) * 0.5
+        for b in range(len(k)):  # keep every base symmetric
+            kb = int(k[b])
+            blk = m[mo[b]:mo[b] + kb * kb].reshape(kb, kb)
+            m[mo[b]:mo[b] + kb * kb] = ((blk + blk.T) / 2).reshape(-1)
+        md = torch.from_numpy(m).to(dev)
+        gd = torch.from_numpy(g).to(dev) if loop else None
+        got = plan.run(md, gamma=gd).cpu().numpy()
+        want = run(dev, m, mo, k, rep, ro, g if loop else None)
+        assert np.array_equal(got, want)  # same schedule, same order of operations
+    plan.close()
+
+
+def test_plan_errors(dev):
+    plan = api.HafnianPlan([0], [2], [1, 1], [0], loop=True)
+    B = torch.eye(2, dtype=torch.complex128, device=dev)
+    with pytest.raises(pq.PQError) as e:
+        plan.run(B)  # a loop plan needs loop weights
+    assert e.value.code == pq.PQ_ERR_ARG
+    with pytest.raises(pq.PQError) as e:
+        api.HafnianPlan([0], [2], [1, -1], [0])
+    assert e.value.code == pq.PQ_ERR_ARG
+    empty = api.HafnianPlan([], [], [], [])
+    assert empty.run(B).numel() == 0
