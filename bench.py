@@ -505,6 +505,17 @@ def extra_measurements(args, dev, stream, flush, peak_tflops, fp64_lane_ops):
     api.bs_sample(Us, s8, order, unif)
     secs = time.perf_counter() - t0
     res["sampler_m16_n8"] = {"samples": 2000, "s": secs, "samples_per_s": 2000 / secs}
+    # a larger sampler run: m = 40 Haar, 20 photons in modes 0..19, 100 samples
+    # (the last steps evaluate 20 minors of size 19, 2^18 terms each, per sample)
+    U40 = torch.from_numpy(W.haar_unitary(40, W.rng_for(7, 1))).to(dev)
+    s20 = np.zeros(40, dtype=np.int32)
+    s20[:20] = 1
+    order20, unif20 = W.sampler_draws(100, 20, 1008)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    api.bs_sample(U40, s20, order20, unif20)
+    secs = time.perf_counter() - t0
+    res["sampler_m40_n20"] = {"samples": 100, "s": secs, "samples_per_s": 100 / secs}
     # lossy boson sampling (Sec. 3.2.4): m = 10 Haar factors V, W, transmissions
     # eta ~ U[0.5, 0.95], 5 photons in modes 0..4, every output pattern with at
     # most 5 photons (3003 patterns, 42504 permanents of the 20-mode dilation);
