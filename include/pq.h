@@ -350,9 +350,9 @@ int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms, void* str
 
 /* ---- Permanent without allocation ---------------------------------------
  * The paper has no counterpart to this call; it exists for callers that
- * cannot allocate device memory: code running while a stream is captured
- * into a CUDA graph (where cudaMalloc is not allowed), code inside a
- * framework whose caching allocator owns the device memory, and
+ * cannot allocate device memory: code inside a framework whose caching
+ * allocator owns the device memory (an allocation of its own can fail or
+ * fragment that pool), processes held to a fixed device-memory budget, and
  * latency-critical paths that cannot pay for the device synchronisation an
  * allocation may cause.
  *
@@ -360,7 +360,9 @@ int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms, void* str
  * kernel, same method) but allocates nothing: the descriptor, the task list,
  * the partial sums and the counters live in a static device array of
  * PQ_NOALLOC_SCRATCH_BYTES that every GPU holds from the moment it loads the
- * library until the process exits.
+ * library until the process exits.  The call plans on the host into a
+ * fixed-size structure and hands it to a set-up kernel by value, so nothing
+ * the host passes has to outlive the call.
  *   B: device, k x l row-major complex; row_mult[k], col_mult[l]: HOST
  *   (read during the call); out: device, one complex.  Asynchronous on stream.
  * Errors: PQ_ERR_ARG (null, negative, sum r != sum c); PQ_ERR_UNSUPPORTED
@@ -369,10 +371,12 @@ int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms, void* str
  * to n = 35 fits);
  * PQ_ERR_CUDA.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every
- * call reuses the same array (the counters are cleared at the start of each
- * call), so calls whose GPU work overlaps -- on two streams or from two host
- * threads -- race with each other: serialise them. */
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use the call after
+ * cudaDeviceReset on that device.  Every call reuses the same array (the
+ * counters are cleared at the start of each call), so calls whose GPU work
+ * overlaps -- on two streams or from two host threads -- race with each
+ * other: serialise them. */
 #define PQ_NOALLOC_SCRATCH_BYTES (1 << 20)
 int pq_permanent_noalloc(const pq_c128* B, int32_t k, int32_t l, const int32_t* row_mult,
                          const int32_t* col_mult, pq_c128* out, void* stream);

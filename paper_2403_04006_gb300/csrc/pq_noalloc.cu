@@ -1,21 +1,24 @@
 // pq_noalloc.cu -- permanent of one base matrix without any memory allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (a device allocation is not allowed there), code
-// embedded in a framework whose caching allocator owns all device memory, and
-// latency-critical paths that cannot afford the implicit device
+// Some callers cannot call cudaMalloc: code embedded in a framework whose
+// caching allocator owns the device memory (a cudaMalloc of its own can fail
+// or fragment that pool), processes that run under a fixed device-memory
+// budget, and latency-critical paths that cannot afford the implicit device
 // synchronisation an allocation may bring.  pq_permanent_noalloc serves them:
 // it runs the same forward kernel as pq_permanent_batched, but every piece of
 // workspace it needs (the permanent's descriptor and integer metadata, its
 // warp-task list, the per-task partial sums and the task counters) lives in
 // one file-scope static device array that is part of the loaded library.
 //
-// The array is shared by every call on a device and keeps the contents of the
-// last call; the counters are cleared at the start of every call.  Calls whose
-// GPU work overlaps (two streams, or two host threads) race on the array, so
-// issue them in one stream or serialise them.  The device address of the array
-// is looked up once per device, on the first call with that device current;
-// make that first call before any stream capture.
+// The host plans the permanent into a fixed-size structure and passes it by
+// value, as a kernel argument, to a set-up kernel that writes it into the
+// array, clears the counters and fills the task list; so no host buffer has
+// to outlive the call.  The array is shared by every call on a device and
+// keeps the contents of the last call.  Calls whose GPU work overlaps (two
+// streams, or two host threads) race on the array, so issue them in one
+// stream or serialise them.  The device address of the array is looked up
+// once per device, on the first call with that device current; make that
+// first call before any stream capture.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -35,21 +38,36 @@ constexpr int64_t kNoAllocMaxTasks = (int64_t)((kNoAllocBytes - kNoAllocHead) / 
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-__global__ void noalloc_fill_tasks(Task* tasks, int64_t ntasks)
+// The workspace head: descriptor, then integer metadata.  Built on the host
+// and handed to noalloc_setup by value.
+struct NoAllocHead {
+    PermDesc desc;
+    int32_t meta[2 * PQ_MAX_DIM + 3 * PQ_MAX_DIM + 3 * PQ_MAX_DIM];
+};
+static_assert(sizeof(NoAllocHead) + 64 <= kNoAllocHead, "workspace head too small");
+static_assert(sizeof(NoAllocHead) % 4 == 0, "head copied as 32-bit words");
+static_assert(sizeof(NoAllocHead) <= 4000, "head must fit the kernel-parameter space");
+
+// Copy the head into the workspace, clear the counters and fill the task
+// list (task q is part q of permanent 0).  Block 0 writes the head and the
+// counters; every block fills its share of the tasks.
+__global__ void noalloc_setup(const NoAllocHead h, unsigned char* base, int32_t* counters,
+                              Task* tasks, int64_t ntasks)
 {
+    if (blockIdx.x == 0) {
+        const int32_t* src = reinterpret_cast<const int32_t*>(&h);
+        int32_t* dst = reinterpret_cast<int32_t*>(base);
+        for (int w = threadIdx.x; w < (int)(sizeof(NoAllocHead) / 4); w += blockDim.x)
+            dst[w] = src[w];
+        if (threadIdx.x < 16)
+            counters[threadIdx.x] = 0;
+    }
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ntasks;
          q += (int64_t)gridDim.x * blockDim.x) {
         tasks[q].perm = 0;
         tasks[q].part = (int32_t)q;
     }
 }
-
-// Host image of the workspace head: descriptor, then integer metadata.
-struct NoAllocHead {
-    PermDesc desc;
-    int32_t meta[2 * PQ_MAX_DIM + 3 * PQ_MAX_DIM + 3 * PQ_MAX_DIM];
-};
-static_assert(sizeof(NoAllocHead) + 64 <= kNoAllocHead, "workspace head too small");
 
 static int noalloc_fail(int code, const char* msg)
 {
@@ -269,11 +287,10 @@ extern "C" int pq_permanent_noalloc(const pq_c128* B, int32_t k, int32_t l,
     Task* tasks_d = reinterpret_cast<Task*>(base + kNoAllocHead);
     double* partials_d = reinterpret_cast<double*>(base + kNoAllocHead + 8 * (size_t)ntasks);
 
-    if (cudaMemcpyAsync(base, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(counters_d, 0, 64, st) != cudaSuccess)
-        return noalloc_fail(PQ_ERR_CUDA, "workspace set-up copy failed");
     const unsigned fill_blocks = (unsigned)((ntasks + 255) / 256 < 1024 ? (ntasks + 255) / 256 : 1024);
-    noalloc_fill_tasks<<<fill_blocks, 256, 0, st>>>(tasks_d, ntasks);
+    noalloc_setup<<<fill_blocks, 256, 0, st>>>(h, base, counters_d, tasks_d, ntasks);
+    if (cudaGetLastError() != cudaSuccess)
+        return noalloc_fail(PQ_ERR_CUDA, "workspace set-up launch failed");
 
     const int ld = h.desc.l > 0 ? h.desc.l : 1;
     const int kmax = h.desc.k > 0 ? h.desc.k : 1;

@@ -4,10 +4,16 @@ oracle on the same seeded inputs.
 
 Tolerance: every term of the sign-vector sum is formed in FP64 from q and l,
 which the Gray walk updates incrementally over at most 1024 steps per chunk,
-and raised to a power <= 24, so a term carries a relative error of a few 1e-12
-at most; the sum is double-double.  The bound used is therefore
-|gpu - oracle| <= 1e-10 * max(|oracle|, sum |terms|), sum |terms| being the
-oracle's own normalised sum of term magnitudes (the scale of the cancellation).
+and raised to a power <= 24, so a term carries a relative error of a few 1e-13
+at most; the sum is double-double.  The GPU error is therefore bounded by a
+few 1e-13 times sum |terms| (the oracle's normalised sum of term magnitudes,
+the scale of the cancellation).  Wherever that bound is below the tolerance
+-- a cancellation ratio sum |terms| / |value| of at most 1e4, which holds for
+every item of the ragged batches and the (2, ..., 2) shapes here (the largest
+ratio is about 600) -- the check is relative: |gpu - oracle| <= 1e-10 |oracle|.
+Exact zeros (odd N) must come out exactly zero.  Only the block-diagonal
+N = 32 case, whose full sum the oracle cannot evaluate and whose ratio is
+about 3e4, is bounded against the scale instead.
 """
 import math
 
@@ -60,8 +66,20 @@ def pack(items):
             cat(reps, np.int32), np.array(ro, dtype=np.int64), cat(gams, np.complex128))
 
 
+KAPPA_MAX = 1e4  # cancellation ratio up to which the relative check applies
+
+
 def check(got, ref, scale, tol=TOL):
-    assert abs(got - ref) <= tol * max(abs(ref), scale), (got, ref, scale)
+    """Relative check where the cancellation allows it (see the module
+    docstring); returns True if it was the relative one."""
+    if ref == 0:
+        assert got == 0, (got, scale)
+        return True
+    if scale <= KAPPA_MAX * abs(ref):
+        assert abs(got - ref) <= tol * abs(ref), (got, ref, scale)
+        return True
+    assert abs(got - ref) <= tol * scale, (got, ref, scale)
+    return False
 
 
 @pytest.mark.parametrize("loop", [False, True])
@@ -77,7 +95,7 @@ def test_ragged_batch_matches_oracle(dev, loop):
             ref, scale = O.lhaf_grouped(B, gam[ro[b]:ro[b] + kb], r, info=True)
         else:
             ref, scale = O.haf_grouped(B, r, info=True)
-        check(got[b], ref, scale)
+        assert check(got[b], ref, scale)
 
 
 @pytest.mark.parametrize("loop", [False, True])
@@ -88,7 +106,7 @@ def test_paper_repetitions_two(dev, loop):
     for b, (B, r, g) in enumerate(items):
         ref, scale = (O.lhaf_grouped(B, g, r, info=True) if loop
                       else O.haf_grouped(B, r, info=True))
-        check(got[b], ref, scale)
+        assert check(got[b], ref, scale)  # relative 1e-10 for every k
 
 
 @pytest.mark.parametrize("loop", [False, True])

@@ -7,9 +7,11 @@ reference's max-norm).  Expected values come from the oracle's gold mode
 (double-double throughout), whose own error bound is checked to be far below
 these tolerances; exact zeros (Hong-Ou-Mandel) are compared absolutely.
 """
+import ctypes
 import math
 import os
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -37,6 +39,12 @@ def dev():
         pytest.skip("no CUDA device")
     pq.load_library()
     return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ragged_pb():
+    """Workload 4 (65536 permanents), generated once for the module."""
+    return W.ragged()
 
 
 def rel_err(x, ref):
@@ -221,10 +229,10 @@ def test_bs_batched_workload(dev):
         assert rel_err(p.cpu().numpy(), p_ref).max() <= 2 * TOL
 
 
-def test_ragged_workload_sampled(dev):
+def test_ragged_workload_sampled(dev, ragged_pb):
     """Workload 4 at full size (65536 permanents, one persistent launch),
     every 16th item checked against the oracle plus every item of n = 20."""
-    pb = W.ragged()
+    pb = ragged_pb
     got, plan = gpu_perms(pb, dev, use_graph=True)
     assert np.isfinite(got).all()
     ns = np.array([int(pb.row_mult[pb.row_off[b]:pb.row_off[b] + pb.k[b]].sum())
@@ -235,6 +243,80 @@ def test_ragged_workload_sampled(dev):
                        sub.col_mult, sub.col_off, gold=True)
     assert rel_err(got[idx], ref).max() <= TOL
     assert plan.stats()["launches_forward"] == 1
+
+
+def test_ragged_workload_plain_sampled(dev, ragged_pb):
+    """Workload 4 by the plain method: 65536 launches, one per permanent, each
+    cut to fill the GPU (the launch set the benchmark times as the plain
+    path); every 64th item against the oracle."""
+    pb = ragged_pb
+    got, plan = gpu_perms(pb, dev, method="plain")
+    assert plan.stats()["launches_forward"] == pb.batch
+    assert np.isfinite(got).all()
+    idx = list(range(0, pb.batch, 64))
+    sub = pb.subset(idx)
+    ref = O.perm_batch(sub.mats, sub.mat_off, sub.k, sub.l, sub.row_mult, sub.row_off,
+                       sub.col_mult, sub.col_off, gold=True)
+    assert rel_err(got[idx], ref).max() <= TOL
+
+
+def product_columns(pb):
+    """Columns on the product side of every item, as the planner orients it
+    (pq_plan_item_info, host only)."""
+    lib = pq.load_library()
+
+    class Info(ctypes.Structure):
+        _fields_ = [("n", ctypes.c_int32), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
+                    ("transposed", ctypes.c_int32), ("ndig", ctypes.c_int32),
+                    ("J", ctypes.c_int32), ("terms", ctypes.c_int64),
+                    ("chunk_len", ctypes.c_int64), ("chunks", ctypes.c_int64),
+                    ("radix", ctypes.c_int32 * 48), ("row_of_digit", ctypes.c_int32 * 48)]
+
+    out = np.zeros(pb.batch, dtype=np.int64)
+    info = Info()
+    for b in range(pb.batch):
+        _, r, c = pb.item(b)
+        r = np.ascontiguousarray(r, dtype=np.int32)
+        c = np.ascontiguousarray(c, dtype=np.int32)
+        assert lib.pq_plan_item_info(len(r), len(c), r.ctypes.data, c.ctypes.data, 0,
+                                     ctypes.byref(info)) == 0
+        out[b] = info.l
+    return out
+
+
+def test_ragged_workload_backward_sampled(dev, ragged_pb):
+    """Backward of workload 4 at full size: the batched plan's launch per
+    product-column class over all 65536 permanents plus the scatter (the
+    launch set the benchmark times), against Laplace-minor permanents (gold)
+    for every 64th item and every item of the widest class present (product
+    columns in (14, 16]; this batch has none wider), at the gradient
+    tolerance."""
+    pb = ragged_pb
+    db = api.DeviceBatch(pb, dev)
+    plan = api.Plan.for_batch(pb)
+    rng = np.random.default_rng(4004)
+    gout = rng.standard_normal(pb.batch) + 1j * rng.standard_normal(pb.batch)
+    g = api.permanent_backward(db, torch.from_numpy(gout).to(dev), plan).cpu().numpy()
+    assert np.isfinite(g).all()
+    lprod = product_columns(pb)
+    assert lprod.max() == 16
+    assert plan.stats()["launches_backward"] == 8 + 1  # classes l <= 2, 4, ..., 16; scatter
+    wide = np.nonzero(lprod > 14)[0].tolist()
+    assert len(wide) >= 16
+    idx = sorted(set(range(0, pb.batch, 64)) | set(wide))
+
+    def minors(b):
+        B, r, c = pb.item(b)
+        return O.perm_grad(B, r, c, gold=True)
+
+    with ThreadPoolExecutor(O.default_threads()) as ex:
+        refs = list(ex.map(minors, idx))
+    for b, G in zip(idx, refs):
+        B, r, c = pb.item(b)
+        ref = gout[b] * np.conj(G)
+        o = int(pb.mat_off[b])
+        got = g[o:o + B.size].reshape(B.shape)
+        assert np.abs(got - ref).max() <= TOLG * np.abs(ref).max(), b
 
 
 def test_single_large_n30(dev):

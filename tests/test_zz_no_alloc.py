@@ -1,26 +1,34 @@
 """pq_permanent_noalloc: the permanent of one base matrix for callers that
-cannot allocate device memory (inside CUDA-graph capture, under a framework's
-caching allocator, on latency-critical paths).  It must give what the regular
-entry point pq_permanent_batched gives, call after call, although every call
-reuses the same static device workspace.
+cannot allocate device memory (code inside a framework whose caching
+allocator owns the device memory, processes held to a fixed device-memory
+budget, latency-critical paths where an allocation may synchronise the
+device).  It must give what the regular entry point pq_permanent_batched
+gives, call after call, although every call reuses the same static device
+workspace, and it must match the oracle within the tolerance of the other
+parity tests.
 
 This file is collected last on purpose, so a run that stops at the first
 failure has already run every other test; it also passes on its own in a
 fresh process.
 """
 import math
+import os
+import sys
 
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O  # noqa: E402
 from paper_2403_04006_gb300 import api, pq  # noqa: E402
 from paper_2403_04006_gb300 import workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10  # the relative tolerance of the parity tests for n <= 20
+TOL30 = 1e-8  # ... and at n = 30
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 @pytest.fixture(scope="module")
@@ -49,20 +57,41 @@ def regular_entry_point(items, dev):
     return api.permanent_batched(api.DeviceBatch(pb, dev), api.Plan.for_batch(pb)).cpu().numpy()
 
 
+def noalloc(B, r, c, dev):
+    """One pq_permanent_noalloc call through the C ABI; the output buffer starts as NaN."""
+    Bd = torch.from_numpy(np.ascontiguousarray(B, dtype=np.complex128)).to(dev)
+    out = torch.full((1,), complex(float("nan"), float("nan")), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    pq.pq_permanent_noalloc(Bd.data_ptr() if Bd.numel() else None, B.shape[0], B.shape[1],
+                            np.asarray(r), np.asarray(c), out.data_ptr(), stream)
+    return out.cpu().numpy()[0]
+
+
 def test_noalloc_matches_regular_entry_point_twice(dev):
     items = cases()
     ref = regular_entry_point(items, dev)
-    stream = torch.cuda.current_stream().cuda_stream
+    gold = [O.perm_ryser(B, r, c, gold=True) for B, r, c in items]
     for _call in range(2):  # the second call reuses the workspace the first left behind
-        for (B, r, c), want in zip(items, ref):
-            Bd = torch.from_numpy(np.ascontiguousarray(B, dtype=np.complex128)).to(dev)
-            out = torch.full((1,), complex(float("nan"), float("nan")), dtype=torch.complex128,
-                             device=dev)
-            pq.pq_permanent_noalloc(Bd.data_ptr() if Bd.numel() else None, B.shape[0],
-                                    B.shape[1], np.asarray(r), np.asarray(c), out.data_ptr(),
-                                    stream)
-            got = out.cpu().numpy()[0]
+        for (B, r, c), want, w_or in zip(items, ref, gold):
+            got = noalloc(B, r, c, dev)
             assert abs(got - want) <= TOL * abs(want), (B.shape, r, c, got, want)
+            assert abs(got - w_or) <= TOL * abs(w_or), (B.shape, r, c, got, w_or)
+
+
+def test_noalloc_large_permanents(dev):
+    """n = 30 against the stored gold value (16384 warp tasks), and n = 31, whose
+    2^30 terms need longer chunks than the default so that the task list fits
+    the static workspace, against the regular entry point; each twice."""
+    sys.path.insert(0, os.path.join(HERE, "golden"))
+    from make_golden import read_matrix_file
+    A, vals = read_matrix_file(os.path.join(HERE, "golden", "single_large_n30.txt"))
+    A31 = W.single_large(31)
+    want31 = regular_entry_point([(A31, [1] * 31, [1] * 31)], dev)[0]
+    for _call in range(2):
+        got30 = noalloc(A, [1] * 30, [1] * 30, dev)
+        assert abs(got30 - vals["per_gold"]) <= TOL30 * abs(vals["per_gold"]), got30
+        got31 = noalloc(A31, [1] * 31, [1] * 31, dev)
+        assert abs(got31 - want31) <= TOL * abs(want31), (got31, want31)
 
 
 def test_noalloc_rejects_bad_and_oversized_input(dev):
