@@ -17,9 +17,22 @@ double-double accumulation, all host cores) on the same batch (by default the
 whole of it, a few seconds per step on 16 host cores) and prints the same line
 with "impl": "reference".
 
-Under torchrun (N > 1) every rank runs the whole batch on its own GPU (weak
-scaling, no collective on the data path); rank 0 prints the line with the
-slowest rank's time.
+Under torchrun (N > 1) the job evaluates a batch of N x 65536 permanents
+split over the ranks: rank r evaluates block r of it (block 0 is the batch
+above, the others the same recipe from their own seed streams), on its own
+GPU, with no collective on the data path (weak scaling: 65536 permanents per
+GPU).  Rank 0 prints the line with the terms of all blocks over the slowest
+rank's time.
+
+Profiling cases (``--workload``; same JSON line, smaller or different work,
+never the benchmark figure): ``ragged4096`` and ``single30`` run the same
+forward on a 4096-permanent batch of the recipe or the n = 30 permanent;
+``ragged4096-backward`` times the backward (one launch per product-column
+class and the scatter) on the 4096-permanent batch; ``hafnian-2x`` and
+``loop-hafnian-2x`` time the repeated (loop) hafnian of a k x k GBS matrix
+with every index repeated twice (``--k``); ``fp64-sweep`` measures the FP64
+pipe (DFMA, DADD, DMUL) against resident warps per SM and independent chains
+per thread.
 """
 from __future__ import annotations
 
@@ -85,8 +98,20 @@ def barrier(device=None):
 
 
 def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
-    """Units all ranks processed divided by the slowest rank's time."""
+    """Units all ranks processed (each the same count) divided by the slowest
+    rank's time."""
     return units_per_rank * world / seconds_max
+
+
+def sum_over_ranks(x: float, device=None) -> float:
+    """The sum of x over the ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
 
 
 # ---------------------------------------------------------------- clocks
@@ -164,19 +189,35 @@ def profiled_traffic():
     return float(b.group(1))
 
 
-def load_workload(name: str):
-    """(PermBatch, description).  'ragged' is the benchmark workload; the
-    others are smaller cases of the same kernel for profiling."""
+PROFILE_CASES = ("ragged4096-backward", "hafnian-2x", "loop-hafnian-2x", "fp64-sweep")
+
+
+def load_workload(name: str, block: int = 0):
+    """(PermBatch, description).  'ragged' is the benchmark workload (block
+    ``block`` of it under torchrun); the others are smaller cases of the same
+    kernel for profiling."""
     from paper_2403_04006_gb300 import workloads as W
     if name == "ragged":
-        return W.ragged(), WORKLOAD
-    if name == "ragged4096":
+        if block == 0:
+            return W.ragged(), WORKLOAD
+        return W.ragged(block=block), WORKLOAD + f", block {block} (own seed streams)"
+    if name in ("ragged4096", "ragged4096-backward"):
         return W.ragged(count=4096), "ragged recipe with 4096 permanents (profiling case)"
     if name == "single30":
         A = W.single_large(30)
         return (W.pack_batch([(A, [1] * 30, [1] * 30)]),
                 "single permanent n = 30, top-left block of a Haar 60 x 60 (seed 1002)")
     raise ValueError(f"unknown workload {name}")
+
+
+def bench_config(desc: str, permanents: int, terms: int, world: int) -> dict:
+    """The workload the line measures; both arms print this same object."""
+    return {"workload": desc, "permanents": permanents, "terms": terms,
+            "parallelism": (f"{world} ranks, block r of a batch of {world} x {permanents} "
+                            "permanents on rank r, no collective on the data path"
+                            if world > 1 else "1 GPU"),
+            "l2": "GPU arm: flushed (256 MB write) before every timed step; "
+                  "CPU arm: inputs in host memory"}
 
 
 def max_sm_clock_mhz(gpu_index: int) -> float:
@@ -260,7 +301,9 @@ def bench_ours(args):
     init_dist("nccl")
     pq.load_library()
 
-    pb, workload_desc = load_workload(args.workload)
+    if args.workload in PROFILE_CASES:
+        return bench_case(args, dev)
+    pb, workload_desc = load_workload(args.workload, block=rank)
     db = api.DeviceBatch(pb, dev)
     plan = api.Plan.for_batch(pb, method="batched", use_graph=True)
     plan.autotune(db)
@@ -307,8 +350,11 @@ def bench_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms_mean = sum(step_ms) / len(step_ms)
     ms_max = max_over_ranks(ms_mean, dev)
-    value = whole_job_rate(st["terms"], world, ms_max * 1e-3)
-    perms_per_s = whole_job_rate(st["permanents"], world, ms_max * 1e-3)
+    # every rank holds its own block: the job's units are the sum over ranks
+    job_terms = sum_over_ranks(st["terms"], dev)
+    job_perms = sum_over_ranks(st["permanents"], dev)
+    value = job_terms / (ms_max * 1e-3)
+    perms_per_s = job_perms / (ms_max * 1e-3)
     achieved_tflops = st["flops_forward"] / (ms_mean * 1e-3) / 1e12
 
     # ---- end to end through the C ABI with host buffers
@@ -336,7 +382,7 @@ def bench_ours(args):
         e2e_step()
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), dev)
-    e2e_value = whole_job_rate(st["terms"], world, e2e_s)
+    e2e_value = job_terms / e2e_s
 
     extra = {}
     if rank == 0 and not args.quick:
@@ -364,11 +410,9 @@ def bench_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc, "permanents": st["permanents"],
-                   "terms": st["terms"],
-                   "method": "batched persistent kernel, CUDA graph, autotuned chunks",
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"dp{world} (independent batches, no collective)"},
+        "config": bench_config(WORKLOAD if args.workload == "ragged" else workload_desc,
+                               int(job_perms), int(job_terms), world),
+        "method": "batched persistent kernel, CUDA graph, autotuned chunks",
         "permanents_per_s": perms_per_s,
         "roofline": {"bound": "alu", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s",
@@ -555,6 +599,87 @@ def extra_measurements(args, dev, stream, flush, peak_tflops, fp64_lane_ops):
     return res
 
 
+def bench_case(args, dev):
+    """One profiling case (PROFILE_CASES): time the operation over --steps
+    launches (L2 flushed before each, CUDA events on the launching stream)
+    and print a JSON line for it."""
+    import torch
+
+    from paper_2403_04006_gb300 import api
+    from paper_2403_04006_gb300 import workloads as W
+
+    stream = torch.cuda.Stream(device=dev)
+    if args.workload == "fp64-sweep":
+        from paper_2403_04006_gb300 import pq
+        hz = max_sm_clock_mhz(dev.index) * 1e6
+        table = {}
+        for op, name in enumerate(("DFMA", "DADD", "DMUL")):
+            for w in (1, 2, 4, 8, 16, 32, 64):
+                table[f"{name} {w} warps/SM"] = {
+                    f"ch{c}": round(pq.pq_probe_fp64_sweep(op, w, c, 1 << 14, stream.cuda_stream)
+                                    / hz, 3) for c in (1, 2, 4, 8)}
+        print(json.dumps({"profiling_case": "fp64-sweep",
+                          "unit": "lane operations per clock per SM at the maximum SM clock",
+                          "sm_max_mhz": hz / 1e6, "table": table}), flush=True)
+        return
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    extra = {}
+    if args.workload == "ragged4096-backward":
+        pb, desc = load_workload(args.workload)
+        db = api.DeviceBatch(pb, dev)
+        plan = api.Plan.for_batch(pb, method="batched")
+        gout = torch.ones(pb.batch, dtype=torch.complex128, device=dev)
+
+        def op():
+            api.permanent_backward(db, gout, plan, stream=stream)
+        terms_of = lambda: plan.stats()["terms"]  # noqa: E731
+        desc = desc.replace("(profiling case)", "backward (profiling case)")
+    else:
+        loop = args.workload.startswith("loop")
+        B, r, g = W.paper_repeated_hafnian(args.k, loop=loop)
+        Bd = torch.from_numpy(B.reshape(-1)).to(dev)
+        gd = torch.from_numpy(g).to(dev) if loop else None
+        hplan = api.HafnianPlan([0], [args.k], r, [0], loop=loop)
+        hout = torch.empty(1, dtype=torch.complex128, device=dev)
+
+        def op():
+            hplan.run(Bd, gamma=gd, out=hout, stream=stream)
+        terms_of = lambda: 2 * 3 ** (args.k - 1)  # noqa: E731
+        desc = (f"{'loop ' if loop else ''}hafnian of a {args.k} x {args.k} GBS matrix, every "
+                f"index repeated twice (N = {2 * args.k}; profiling case)")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            op()
+    stream.synchronize()
+    ms = []
+    torch.cuda.nvtx.range_push("timed_region")
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            e0.record(stream)
+            op()
+            e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
+    if args.workload == "ragged4096-backward":
+        st = plan.stats()
+        extra = {"fp64_instr_backward": st["fp64_instr_backward"],
+                 "launches": st["launches_backward"]}
+    mean = sum(ms) / len(ms)
+    terms = terms_of()
+    print(json.dumps({
+        "metric": METRIC, "value": terms / (mean * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "profiling_case": args.workload,
+        "config": {"workload": desc, "terms": terms,
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "ms_per_launch_set": ms, "extra": extra}), flush=True)
+
+
 # ---------------------------------------------------------------- reference arm
 def bench_reference(args):
     rank, world, _ = rank_env()
@@ -567,6 +692,11 @@ def bench_reference(args):
     threads = host_cores()
     idx = oracle_sample(pb, args.cpu_sample_terms)
     terms = glynn_terms(pb, idx)
+    # the job the GPU arm measures: blocks 0 .. world-1 (the oracle times block 0)
+    job_terms = glynn_terms(pb, range(pb.batch))
+    for blk in range(1, world):
+        bs = W.ragged(block=blk, sizes_only=True)
+        job_terms += glynn_terms(bs, range(bs.batch))
     for _ in range(args.warmup):
         run_oracle_sample(pb, idx[: max(1, len(idx) // 8)], threads)
     secs = [run_oracle_sample(pb, idx, threads) for _ in range(args.steps)]
@@ -577,10 +707,12 @@ def bench_reference(args):
         "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORKLOAD, "sample_permanents": len(idx), "sample_terms": terms},
+        "config": bench_config(WORKLOAD, pb.batch * world, int(job_terms), world),
+        "method": "CPU oracle: Ryser FP64 + double-double accumulation, all host cores",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{len(idx)} of {pb.batch} permanents per step, "
-                                   f"Ryser FP64 + double-double accumulation, {cpu_model()}"},
+                         "sample": f"{len(idx)} of {pb.batch} permanents per step "
+                                   f"({terms} Gray-code terms), Ryser FP64 + double-double "
+                                   f"accumulation, {cpu_model()}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -593,8 +725,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the extra measurements")
-    ap.add_argument("--workload", choices=["ragged", "ragged4096", "single30"], default="ragged",
-                    help="ragged is the benchmark; the others are profiling cases")
+    ap.add_argument("--workload", choices=["ragged", "ragged4096", "single30", *PROFILE_CASES],
+                    default="ragged", help="ragged is the benchmark; the others are profiling cases")
+    ap.add_argument("--k", type=int, default=18,
+                    help="hafnian profiling cases: base size k (N = 2k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-terms", type=float, default=math.inf,
                     help="Ryser terms of the oracle sample (default: the whole batch, "

@@ -163,6 +163,25 @@ int pq_permanent_batched(const pq_batch* b, pq_c128* out, pq_plan* plan, void* s
  * other sizes), PQ_ERR_CUDA. */
 int pq_permanent_partials(const pq_batch* b, double* partials, pq_plan* plan, void* stream);
 
+/* The exchange step of a permanent batch split over ranks: combines the
+ * shards' partial sums written by pq_permanent_partials into permanents,
+ * out[p] = 2^{-(n[p]-1)} * sum over shards r = 0 .. nshards-1, in that order,
+ * of parts[r][p] (double-double additions: TwoSum of the high parts, errors
+ * and low parts gathered into the low part; no scaling for n[p] = 0).  This
+ * is the normalisation of the BB/FG formula (Sec. 4.2) applied once to the
+ * whole sum.  parts: nshards x batch x 4 doubles (re hi, re lo, im hi, im
+ * lo), shard-major, as an all-gather of each shard's partials lays them out;
+ * n: photons of each permanent (int32, batch); out: batch complex.
+ * pq_combine_partials takes DEVICE pointers and runs one kernel on `stream`
+ * (asynchronous, allocates nothing); pq_combine_partials_host takes HOST
+ * pointers, needs no GPU and gives the same bits.  Errors: PQ_ERR_ARG (null
+ * pointer with batch > 0, batch < 0, nshards < 1; on the host also n outside
+ * [0, PQ_MAX_N]), PQ_ERR_CUDA. */
+int pq_combine_partials(const double* parts, int32_t nshards, int64_t batch, const int32_t* n,
+                        pq_c128* out, void* stream);
+int pq_combine_partials_host(const double* parts, int32_t nshards, int64_t batch,
+                             const int32_t* n, pq_c128* out);
+
 /* Boson-sampling probabilities, Eq. (BS_prob).  U: device, m x m, U[out][in];
  * input_occ: device, m; output_occ: device, B x m; probs: device, B doubles;
  * amps: device, B complex, nullable -- receives per(U_{s,t}) (needed by the
@@ -307,6 +326,49 @@ int pq_loop_hafnian_repeated(const pq_c128* mats, const pq_c128* gamma, const in
  * boson-sampling plan pass b = NULL and U (device) instead. */
 int pq_autotune(pq_plan* plan, const pq_batch* b, const pq_c128* U, void* stream);
 
+/* The process-wide tuning table: entry n (n = 0 .. PQ_MAX_N) is the Gray-code
+ * chunk length, as log2 of the number of terms, that later plans use for
+ * permanents of n photons (0: the built-in default); pq_autotune fills it.
+ * host arrays of PQ_MAX_N + 1 int32; set rejects entries outside [0, 30]
+ * (PQ_ERR_ARG).  Every shard of a split permanent batch (pq_plan_options
+ * shard_count > 1) must be planned under the same table: planning reads it,
+ * so shards planned under different tables cut the Gray code differently
+ * and their partials do not add up.  No GPU needed. */
+int pq_tune_table_get(int32_t* log2);
+int pq_tune_table_set(const int32_t* log2);
+
+/* Tuning cache on disk: a JSON file {"format": ..., "tables": {"<device
+ * key>": [PQ_MAX_N + 1 ints], ...}} holding one tuning table per GPU model.
+ * pq_tune_cache_save writes the current table under device_key (NULL: the
+ * current device's name and SM count, which needs a GPU), keeping the other
+ * keys of an existing file; the file is replaced atomically.
+ * pq_tune_cache_load sets the table from the entry of device_key (same
+ * default) and reports in *found whether the file had one (a missing file is
+ * not an error: *found = 0).  Planning itself never touches the file.
+ * Errors: PQ_ERR_ARG (null, unreadable or malformed file, bad table),
+ * PQ_ERR_CUDA (no device to name the key). */
+int pq_tune_cache_save(const char* path, const char* device_key);
+int pq_tune_cache_load(const char* path, const char* device_key, int32_t* found);
+
+/* Device error record of a plan.  Before using a warp task, the forward and
+ * backward kernels check it and the descriptor it names against the launch:
+ * the permanent index, the task's part, the base sizes against the launch's
+ * shared-memory layout, the digit counts against the Gray walk's limits, and
+ * the descriptor's indices into the plan's metadata, partial sums and
+ * outputs.  A task that fails is skipped (its permanent's output is left
+ * unwritten) and the first failure is kept.  This call reads the record
+ * (it synchronises the device): *code receives 0 or a PQ_DEVERR_* code,
+ * *task the index of the failing task in the launch's task list; clear != 0
+ * resets the record.  The synchronous calls (plan == NULL) read it
+ * themselves and return PQ_ERR_STATE when it is set.  No device wait exists
+ * in the library, so PQ_ERR_TIMEOUT is never returned. */
+#define PQ_DEVERR_TASK_PERM 1   /* task names a permanent outside the batch          */
+#define PQ_DEVERR_TASK_PART 2   /* task part outside its permanent's range             */
+#define PQ_DEVERR_LAYOUT 3      /* base sizes beyond the launch's shared-memory layout */
+#define PQ_DEVERR_DIGITS 4      /* digit counts beyond the walk's limits               */
+#define PQ_DEVERR_INDEX 5       /* metadata, partial-sum or output index out of range  */
+int pq_plan_device_error(pq_plan* plan, int32_t* code, int64_t* task, int32_t clear);
+
 /* Statistics of a plan, host memory: number of permanents, total Gray-code
  * terms, algorithmic FP64 flops of one forward execution (FMA = 2; the count
  * of a straightforward Glynn evaluation: 2l + 6(n-1) + 2 per term, +2 for a
@@ -348,6 +410,16 @@ int pq_plan_get_stats(const pq_plan* plan, pq_plan_stats* out);
  * the paper's method; it provides the roofline denominator. */
 int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms, void* stream);
 
+/* FP64 pipe sweep: op 0 = DFMA, 1 = DADD, 2 = DMUL; `warps_per_sm` resident
+ * warps on every SM (1 .. 64), each thread running `chains` (1, 2, 4 or 8)
+ * independent dependency chains of that instruction for 4 x iters steps.
+ * Writes the measured lane operations per second per SM (divide by the SM
+ * clock for operations per clock).  Synchronises `stream`.  Measures the
+ * chip: how many warps saturate the FP64 pipe and whether dependency
+ * latency matters, which fixes the layout of the kernels. */
+int pq_probe_fp64_sweep(int32_t op, int32_t warps_per_sm, int32_t chains, int64_t iters,
+                        double* lane_ops_per_sm_per_s, void* stream);
+
 /* ---- Permanent without allocation ---------------------------------------
  * The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory: code inside a framework whose caching
@@ -380,6 +452,22 @@ int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms, void* str
 #define PQ_NOALLOC_SCRATCH_BYTES (1 << 20)
 int pq_permanent_noalloc(const pq_c128* B, int32_t k, int32_t l, const int32_t* row_mult,
                          const int32_t* col_mult, pq_c128* out, void* stream);
+
+/* ---- Test hooks ----------------------------------------------------------
+ * pq_debug_fail_allocation(after): the allocation that follows `after`
+ * successful ones -- device buffers and the host plan objects the library
+ * creates -- reports failure (PQ_ERR_NOMEM from the call that made it), once;
+ * after < 0 disarms the hook.  pq_debug_live_allocations: the device buffers
+ * and plan objects the library currently holds (a call that fails must leave
+ * both where they were).  pq_debug_corrupt_plan(plan, what) overwrites the
+ * plan's device-side schedule so that the kernels' guards have something to
+ * catch: what = 1, the first task of each task list names permanent
+ * batch + 5; what = 2, permanent 0's descriptor gets more product columns
+ * than the launch's layout holds.  The host copy is left alone; destroy the
+ * plan afterwards.  The hooks need no GPU except pq_debug_corrupt_plan. */
+int pq_debug_fail_allocation(int64_t after);
+int pq_debug_live_allocations(int64_t* device_buffers, int64_t* host_objects);
+int pq_debug_corrupt_plan(pq_plan* plan, int32_t what);
 
 /* ---- Diagnostics (host only; no GPU needed) ---------------------------- */
 

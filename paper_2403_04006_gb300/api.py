@@ -166,54 +166,66 @@ def permanent_partials(db: DeviceBatch, plan: Plan, out: torch.Tensor | None = N
     return out
 
 
-def _two_sum(a: np.ndarray, b: np.ndarray):
-    s = a + b
-    bb = s - a
-    return s, (a - (s - bb)) + (b - bb)
-
-
 def combine_partials(parts, n) -> np.ndarray:
-    """Permanents from the shards' partial sums: the (batch, 4) arrays are
-    added in the order given with TwoSum on the high parts (double-double)
-    and scaled by 2^{-(n-1)} (n = 0: no scaling).  ``n`` holds each
-    permanent's photon number."""
-    parts = [np.asarray(p, dtype=np.float64) for p in parts]
-    rh, rl = parts[0][:, 0].copy(), parts[0][:, 1].copy()
-    ih, il = parts[0][:, 2].copy(), parts[0][:, 3].copy()
-    for p in parts[1:]:
-        rh, e = _two_sum(rh, p[:, 0])
-        rl = rl + p[:, 1] + e
-        ih, e = _two_sum(ih, p[:, 2])
-        il = il + p[:, 3] + e
-    n = np.asarray(n, dtype=np.int64)
-    shift = np.where(n > 0, 1 - n, 0)
-    return np.ldexp(rh + rl, shift) + 1j * np.ldexp(ih + il, shift)
+    """Permanents from the shards' partial sums (host arrays of shape
+    (batch, 4), in shard order) and each permanent's photon number ``n``:
+    the library adds them in double-double and scales by 2^{-(n-1)}
+    (pq_combine_partials_host)."""
+    stacked = np.stack([np.asarray(p, dtype=np.float64) for p in parts])
+    return _pq.pq_combine_partials_host(stacked, np.asarray(n))
+
+
+def combine_partials_device(parts: torch.Tensor, n: torch.Tensor, out: torch.Tensor | None = None,
+                            stream=None) -> torch.Tensor:
+    """The same on the GPU (pq_combine_partials): ``parts`` a (nshards,
+    batch, 4) float64 CUDA tensor, ``n`` an int32 CUDA tensor of photon
+    numbers; returns the complex128 permanents on the same device."""
+    parts = parts.contiguous()
+    n32 = n.to(torch.int32).contiguous()
+    batch = parts.shape[1]
+    if out is None:
+        out = torch.empty(batch, dtype=torch.complex128, device=parts.device)
+    _pq.pq_combine_partials(_ptr(parts) if batch else None, parts.shape[0], batch,
+                            _ptr(n32) if batch else None, _ptr(out) if batch else None,
+                            _stream_handle(stream))
+    return out
 
 
 def gather_partials(local: torch.Tensor, group=None) -> list:
     """Every shard's partials, in rank order, on every rank (one all_gather of
-    32 bytes per permanent: the exchange step of a split permanent).
-    Without an initialised process group this rank's partials alone."""
+    32 bytes per permanent: the exchange step of a split permanent), as a
+    list of tensors on the device of ``local`` when the backend is NCCL, on
+    the CPU otherwise.  Without an initialised process group, this rank's
+    partials alone."""
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()):
-        return [local.cpu().numpy()]
+        return [local]
     world = dist.get_world_size(group)
     t = local if dist.get_backend(group) == "nccl" else local.cpu()
     bufs = [torch.empty_like(t) for _ in range(world)]
     dist.all_gather(bufs, t.contiguous(), group=group)
-    return [b.cpu().numpy() for b in bufs]
+    return bufs
 
 
-def permanent_distributed(db: DeviceBatch, plan: Plan, group=None, stream=None) -> np.ndarray:
+def photon_numbers(pb: PermBatch) -> np.ndarray:
+    """n of every permanent of a batch (the sum of its row multiplicities)."""
+    return np.array([int(pb.row_mult[pb.row_off[b]:pb.row_off[b] + pb.k[b]].sum())
+                     for b in range(pb.batch)], dtype=np.int32)
+
+
+def permanent_distributed(db: DeviceBatch, plan: Plan, group=None, stream=None) -> torch.Tensor:
     """Permanents of a batch whose Gray codes are split over the ranks of a
     process group: each rank passes the plan of its shard (``shard=(rank,
-    world)``); returns the complex permanents on every rank."""
+    world)``, all planned under the same tuning table); every rank gets the
+    complex permanents, combined by the library from the all-gathered
+    partials (on the GPU with NCCL, on the host otherwise)."""
     part = permanent_partials(db, plan, stream=stream)
-    torch.cuda.synchronize(db.mats.device)
-    host = db.host
-    n = np.array([int(host.row_mult[host.row_off[b]:host.row_off[b] + host.k[b]].sum())
-                  for b in range(host.batch)], dtype=np.int64)
-    return combine_partials(gather_partials(part, group), n)
+    parts = gather_partials(part, group)
+    n = photon_numbers(db.host)
+    if parts[0].is_cuda:
+        return combine_partials_device(torch.stack(parts),
+                                       torch.from_numpy(n).to(parts[0].device), stream=stream)
+    return torch.from_numpy(combine_partials([p.numpy() for p in parts], n))
 
 
 def permanent_backward(db: DeviceBatch, grad_out: torch.Tensor, plan: Plan | None = None,

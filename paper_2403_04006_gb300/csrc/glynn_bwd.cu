@@ -395,7 +395,31 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
     }
 }
 
-__global__ void __launch_bounds__(256) glynn_bwd_kernel(BwdArgs a, int64_t t_begin,
+// The guards of task ti (those of the forward with the class's low-digit
+// bound jb, and at most n2 product columns with multiplicity >= 2, for which
+// the launch keeps powers per lane; they come first, the columns being
+// sorted by non-increasing multiplicity).  Returns 0 or the error code.
+__device__ __forceinline__ int32_t bwd_guard(const BwdArgs& a, int64_t ti, int kmax, int ld, int jb,
+                                          int n2)
+{
+    const Task t = a.tasks[ti];
+    const int32_t bad = task_guard(t, a.desc, a.nperm, a.nmeta, -1, kmax, ld, jb);
+    if (bad)
+        return bad;
+    const PermDesc D = a.desc[t.perm];
+    const int32_t* cm = a.meta + D.meta + 2 * D.k + D.l;  // cmul
+    int rep = 0;
+    while (rep < D.l && cm[rep] >= 2)
+        ++rep;
+    return rep > n2 ? kErrDescLayout : 0;
+}
+
+// Tasks [t_begin, t_end) of the list; a task whose guards fail is skipped
+// and recorded in the error record.
+// At least 3 blocks of 256 threads per SM caps the kernel at 85 registers per
+// thread; it needs 80 without spilling, and without the cap the guards' extra
+// branch in the task loop lets the allocator take 104.
+__global__ void __launch_bounds__(256, 3) glynn_bwd_kernel(BwdArgs a, int64_t t_begin,
                                                          int64_t t_end, int kmax, int ld, int jb,
                                                          int n2, int queue)
 {
@@ -405,8 +429,15 @@ __global__ void __launch_bounds__(256) glynn_bwd_kernel(BwdArgs a, int64_t t_beg
     int staged = -1;
     if (!queue) {
         const int64_t ti = t_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-        if (ti < t_end)
-            bwd_task(a, a.tasks[ti], sm, staged, lane);
+        if (ti >= t_end)
+            return;
+        const int32_t bad = bwd_guard(a, ti, kmax, ld, jb, n2);
+        if (bad) {
+            if (lane == 0)
+                record_error(a.err, bad, ti);
+            return;
+        }
+        bwd_task(a, a.tasks[ti], sm, staged, lane);
         return;
     }
     for (;;) {
@@ -417,6 +448,12 @@ __global__ void __launch_bounds__(256) glynn_bwd_kernel(BwdArgs a, int64_t t_beg
         const int64_t ti = t_begin + q;
         if (ti >= t_end)
             break;
+        const int32_t bad = bwd_guard(a, ti, kmax, ld, jb, n2);
+        if (bad) {
+            if (lane == 0)
+                record_error(a.err, bad, ti);
+            continue;
+        }
         bwd_task(a, a.tasks[ti], sm, staged, lane);
     }
 }

@@ -319,6 +319,21 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
         finalize(a, D, tot);
 }
 
+// Task ti of the list, once its guards pass (a failing task is skipped and
+// recorded in the error record).
+__device__ __forceinline__ void run_task(const ExecArgs& a, int64_t ti, WarpSmem& sm, int kmax,
+                                         int ld, int& staged, int lane)
+{
+    const Task t = a.tasks[ti];
+    const int32_t bad = task_guard(t, a.desc, a.nperm, a.nmeta, a.nslots, kmax, ld, kMaxLowDigits);
+    if (bad) {
+        if (lane == 0)
+            record_error(a.err, bad, ti);
+        return;
+    }
+    process_task(a, t, sm, staged, lane);
+}
+
 // Tasks [t_begin, t_end) of the list.  queue != 0: every warp pulls tasks from
 // the global counter until the range is exhausted (persistent launch of a
 // whole batch); queue == 0: warp w of block b takes task t_begin + b * wpb + w
@@ -334,7 +349,7 @@ __global__ void __launch_bounds__(256) glynn_fwd_kernel(ExecArgs a, int64_t t_be
     if (!queue) {
         const int64_t ti = t_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
         if (ti < t_end)
-            process_task(a, a.tasks[ti], sm, staged, lane);
+            run_task(a, ti, sm, kmax, ld, staged, lane);
         return;
     }
     for (;;) {
@@ -345,7 +360,7 @@ __global__ void __launch_bounds__(256) glynn_fwd_kernel(ExecArgs a, int64_t t_be
         const int64_t ti = t_begin + q;
         if (ti >= t_end)
             break;
-        process_task(a, a.tasks[ti], sm, staged, lane);
+        run_task(a, ti, sm, kmax, ld, staged, lane);
     }
 }
 

@@ -547,13 +547,14 @@ static void haf_plan_free(pq_haf_plan* P)
 {
     if (!P)
         return;
-    cudaFree(P->desc_d);
-    cudaFree(P->meta_d);
-    cudaFree(P->tasks_d);
-    cudaFree(P->part_d);
-    cudaFree(P->cnt_d);
-    cudaFree(P->loopc_d);
+    dev_free(P->desc_d);
+    dev_free(P->meta_d);
+    dev_free(P->tasks_d);
+    dev_free(P->part_d);
+    dev_free(P->cnt_d);
+    dev_free(P->loopc_d);
     delete P;
+    host_object_freed();
 }
 
 // Plan: digits, chunks, tasks (longest first), loop-polynomial factors;
@@ -721,9 +722,13 @@ static int haf_plan_build(const int64_t* mat_off, const int32_t* k, const int32_
         }
         slot += (int32_t)nt;
     }
-    pq_haf_plan* P = new (std::nothrow) pq_haf_plan();
-    if (!P)
+    if (!host_object_alloc_ok())
         return report(PQ_ERR_NOMEM, "host allocation failed");
+    pq_haf_plan* P = new (std::nothrow) pq_haf_plan();
+    if (!P) {
+        host_object_freed();
+        return report(PQ_ERR_NOMEM, "host allocation failed");
+    }
     P->loop = loop ? 1 : 0;
     P->batch = batch;
     if (batch == 0) {
@@ -742,15 +747,15 @@ static int haf_plan_build(const int64_t* mat_off, const int32_t* k, const int32_
     P->kmax = kmax;
     P->jmax = jmax;
     int rc = PQ_OK;
-    if (cudaMalloc((void**)&P->loopc_d, sizeof(double) * std::max<size_t>(loopc.size(), 1)) !=
+    if (dev_alloc((void**)&P->loopc_d, sizeof(double) * std::max<size_t>(loopc.size(), 1)) !=
             cudaSuccess ||
-        cudaMalloc((void**)&P->desc_d, sizeof(HafDesc) * batch) != cudaSuccess ||
-        cudaMalloc((void**)&P->meta_d, sizeof(int32_t) * std::max<size_t>(meta.size(), 1)) !=
+        dev_alloc((void**)&P->desc_d, sizeof(HafDesc) * batch) != cudaSuccess ||
+        dev_alloc((void**)&P->meta_d, sizeof(int32_t) * std::max<size_t>(meta.size(), 1)) !=
             cudaSuccess ||
-        cudaMalloc((void**)&P->tasks_d, sizeof(Task) * sorted.size()) != cudaSuccess ||
-        cudaMalloc((void**)&P->part_d, sizeof(double) * 4 * std::max<int32_t>(slot, 1)) !=
+        dev_alloc((void**)&P->tasks_d, sizeof(Task) * sorted.size()) != cudaSuccess ||
+        dev_alloc((void**)&P->part_d, sizeof(double) * 4 * std::max<int32_t>(slot, 1)) !=
             cudaSuccess ||
-        cudaMalloc((void**)&P->cnt_d, sizeof(int32_t) * (batch + 1)) != cudaSuccess)
+        dev_alloc((void**)&P->cnt_d, sizeof(int32_t) * (batch + 1)) != cudaSuccess)
         rc = report(PQ_ERR_NOMEM, "hafnian workspace allocation failed");
     if (rc == PQ_OK &&
         (cudaMemcpy(P->desc_d, desc.data(), sizeof(HafDesc) * batch, cudaMemcpyHostToDevice) !=

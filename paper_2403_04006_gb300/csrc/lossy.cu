@@ -136,9 +136,9 @@ extern "C" int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c
     double2* Ubig = nullptr;
     double* pbig = nullptr;
     int64_t* first_d = nullptr;
-    if (cudaMalloc((void**)&Ubig, sizeof(double2) * 4 * m * m) != cudaSuccess ||
-        cudaMalloc((void**)&pbig, sizeof(double) * NB) != cudaSuccess ||
-        cudaMalloc((void**)&first_d, sizeof(int64_t) * (B + 1)) != cudaSuccess) {
+    if (dev_alloc((void**)&Ubig, sizeof(double2) * 4 * m * m) != cudaSuccess ||
+        dev_alloc((void**)&pbig, sizeof(double) * NB) != cudaSuccess ||
+        dev_alloc((void**)&first_d, sizeof(int64_t) * (B + 1)) != cudaSuccess) {
         rc = report(PQ_ERR_NOMEM, "lossy workspace allocation failed");
     }
     if (rc == PQ_OK &&
@@ -160,9 +160,9 @@ extern "C" int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
             rc = report(PQ_ERR_CUDA, "lossy marginal failed");
     }
-    cudaFree(Ubig);
-    cudaFree(pbig);
-    cudaFree(first_d);
+    dev_free(Ubig);
+    dev_free(pbig);
+    dev_free(first_d);
     pq_plan_destroy(P);
     return rc;
 }

@@ -38,6 +38,14 @@ static int fail(int code, const char* fmt, ...)
     return code;
 }
 
+#define PQ_ALLOC(pp, bytes)                                                             \
+    do {                                                                                \
+        cudaError_t e_ = dev_alloc((void**)(pp), (bytes));                              \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(PQ_ERR_NOMEM, "device allocation of %zu bytes failed: %s",      \
+                        (size_t)(bytes), cudaGetErrorString(e_));                       \
+    } while (0)
+
 #define PQ_CUDA(call)                                                                   \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \
@@ -51,25 +59,6 @@ namespace pqi {
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace pqi
 extern "C" const char* pq_version(void) { return "pq-gb300 0.1 (sm_103a)"; }
-
-// ---------------------------------------------------------------- tuning table
-// Process-wide chunk length (log2) per photon number (size class), filled by
-// pq_autotune and read by later plans.
-static std::mutex g_tune_mu;
-static int g_tune[PQ_MAX_N + 1] = {0};
-
-static int tune_get(int n)
-{
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    return (n < 0 || n > PQ_MAX_N) ? 0 : g_tune[n];
-}
-
-static void tune_set(int n, int v)
-{
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (n >= 0 && n <= PQ_MAX_N)
-        g_tune[n] = v;
-}
 
 // ---------------------------------------------------------------- planning
 static const int64_t kMaxTerms = int64_t(1) << 62;
@@ -329,11 +318,11 @@ static int default_log2_for(const pq_plan* P, const ItemPlan& it)
 {
     if (P->opts.chunk_log2 > 0)
         return P->opts.chunk_log2;
-    // The shards of a permanent must cut its Gray code identically, whatever
-    // each process has tuned: sharded plans use the fixed default.
-    if (P->opts.shard_count > 0)
-        return 10;
-    if (it.n >= 0 && it.n < (int)P->class_log2.size() && P->class_log2[it.n] > 0)
+    // The shards of a permanent must cut its Gray code identically: a sharded
+    // plan reads only the process-wide table, which every shard must share
+    // (pq_tune_table_set / pq_tune_cache_load).
+    if (P->opts.shard_count == 0 && it.n >= 0 && it.n < (int)P->class_log2.size() &&
+        P->class_log2[it.n] > 0)
         return P->class_log2[it.n];
     int tuned = tune_get(it.n);
     if (tuned > 0)
@@ -345,13 +334,14 @@ template <typename T>
 static int dev_upload(T** dst, const std::vector<T>& src)
 {
     if (*dst) {
-        cudaFree(*dst);
+        dev_free(*dst);
         *dst = nullptr;
     }
     size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
-    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    cudaError_t e = dev_alloc((void**)dst, bytes);
     if (e != cudaSuccess)
-        return fail(PQ_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return fail(PQ_ERR_NOMEM, "device allocation of %zu bytes failed: %s", bytes,
+                    cudaGetErrorString(e));
     if (!src.empty()) {
         e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
         if (e != cudaSuccess)
@@ -367,12 +357,10 @@ static void free_plan_device(pq_plan* P)
                     P->gpart_off_d,   P->grad_local_d,     P->grad_local_off_d, P->item_mat_off_d,
                     P->item_k_d,      P->item_l_d,         P->grad_out_tmp_d, P->bs_pos_d};
     for (void* p : ptrs)
-        if (p)
-            cudaFree(p);
+        dev_free(p);
     void* bptrs[] = {P->desc_bwd_d, P->tasks_bwd_plain_d, P->tasks_bwd_batched_d};
     for (void* p : bptrs)
-        if (p)
-            cudaFree(p);
+        dev_free(p);
     P->desc_bwd_d = nullptr;
     P->tasks_bwd_plain_d = P->tasks_bwd_batched_d = nullptr;
     P->bwd_ready = false;
@@ -466,11 +454,17 @@ static int schedule_and_upload(pq_plan* P)
         const int64_t nt_all = it.trivial ? 1 : (it.nchunks + kWarp - 1) / kWarp;
         if (nt_all > (int64_t(1) << 30))
             return fail(PQ_ERR_UNSUPPORTED, "too many tasks for one permanent");
-        // a sharded plan keeps the contiguous part range of its shard
+        // A sharded plan keeps one contiguous part range of every permanent.
+        // The ranges are cut in R equal pieces, and permanent p gives piece
+        // (shard_index + p) mod R to this shard: a permanent with fewer tasks
+        // than shards then lands on a different shard for each p, instead of
+        // always on the last one.
         int64_t q0 = 0, q1 = nt_all;
         if (P->opts.shard_count > 1) {
-            q0 = nt_all * P->opts.shard_index / P->opts.shard_count;
-            q1 = nt_all * (P->opts.shard_index + 1) / P->opts.shard_count;
+            const int64_t R = P->opts.shard_count;
+            const int64_t piece = (P->opts.shard_index + p) % R;
+            q0 = nt_all * piece / R;
+            q1 = nt_all * (piece + 1) / R;
         }
         const int64_t nt = q1 - q0;
         D.ntasks = (int32_t)nt;
@@ -550,17 +544,16 @@ static int schedule_and_upload(pq_plan* P)
         return rc;
     if ((rc = dev_upload(&P->tasks_batched_d, P->tasks_batched_h)) != PQ_OK)
         return rc;
-    if (P->partials_d)
-        cudaFree(P->partials_d);
+    dev_free(P->partials_d);
     P->partials_d = nullptr;
-    PQ_CUDA(cudaMalloc((void**)&P->partials_d, std::max<size_t>(slot, 1) * 4 * sizeof(double)));
-    if (P->counters_d)
-        cudaFree(P->counters_d);
+    P->nslots = slot;
+    PQ_ALLOC(&P->partials_d, std::max<size_t>(slot, 1) * 4 * sizeof(double));
+    dev_free(P->counters_d);
     P->counters_d = nullptr;
-    PQ_CUDA(cudaMalloc((void**)&P->counters_d, (size_t)(np + 1) * sizeof(int32_t)));
+    PQ_ALLOC(&P->counters_d, (size_t)(np + 1) * sizeof(int32_t));
     if (!P->err_d) {
-        PQ_CUDA(cudaMalloc((void**)&P->err_d, sizeof(int32_t)));
-        PQ_CUDA(cudaMemset(P->err_d, 0, sizeof(int32_t)));
+        PQ_ALLOC(&P->err_d, 2 * sizeof(int32_t));
+        PQ_CUDA(cudaMemset(P->err_d, 0, 2 * sizeof(int32_t)));
     }
     cudaError_t e = fwd_prepare(P->lmax, P->wpb * per_warp);
     if (e != cudaSuccess)
@@ -570,6 +563,26 @@ static int schedule_and_upload(pq_plan* P)
         P->graph = nullptr;
     }
     return PQ_OK;
+}
+
+// Plan objects are counted like device buffers (pq_debug_live_allocations),
+// and the allocation-failure test hook applies to them as well.
+static pq_plan* plan_new()
+{
+    if (!host_object_alloc_ok())
+        return nullptr;
+    pq_plan* P = new (std::nothrow) pq_plan();
+    if (!P)
+        host_object_freed();
+    return P;
+}
+
+static void plan_delete(pq_plan* P)
+{
+    if (!P)
+        return;
+    delete P;
+    host_object_freed();
 }
 
 static int plan_common_init(pq_plan* P, const pq_plan_options* opts)
@@ -606,12 +619,12 @@ extern "C" int pq_plan_create(const pq_batch_sizes* sz, const pq_plan_options* o
         return fail(PQ_ERR_ARG, "null size array");
     if (sz->batch > (int64_t(1) << 30))
         return fail(PQ_ERR_UNSUPPORTED, "batch above 2^30");
-    pq_plan* P = new (std::nothrow) pq_plan();
+    pq_plan* P = plan_new();
     if (!P)
         return fail(PQ_ERR_NOMEM, "host allocation failed");
     int rc = plan_common_init(P, opts);
     if (rc != PQ_OK) {
-        delete P;
+        plan_delete(P);
         return rc;
     }
     P->kind = 0;
@@ -622,13 +635,13 @@ extern "C" int pq_plan_create(const pq_batch_sizes* sz, const pq_plan_options* o
     int64_t off = 0;
     for (int64_t b = 0; b < sz->batch; ++b) {
         if (sz->row_off[b] < 0 || sz->col_off[b] < 0 || sz->mat_off[b] < 0) {
-            delete P;
+            plan_delete(P);
             return fail(PQ_ERR_ARG, "negative offset at item %lld", (long long)b);
         }
         rc = build_item(sz->row_mult + sz->row_off[b], sz->col_mult + sz->col_off[b], sz->k[b],
                         sz->l[b], sz->mat_off[b], sz->l[b], P->items[b]);
         if (rc != PQ_OK) {
-            delete P;
+            plan_delete(P);
             return fail(rc, "item %lld: %s", (long long)b, g_err.c_str());
         }
         P->item_mat_off[b] = sz->mat_off[b];
@@ -641,7 +654,7 @@ extern "C" int pq_plan_create(const pq_batch_sizes* sz, const pq_plan_options* o
     rc = schedule_and_upload(P);
     if (rc != PQ_OK) {
         free_plan_device(P);
-        delete P;
+        plan_delete(P);
         return rc;
     }
     *out = P;
@@ -679,12 +692,12 @@ extern "C" int pq_plan_create_bs(int32_t m, const int32_t* in_occ, const int32_t
     }
     if (opts && opts->shard_count > 1)
         return fail(PQ_ERR_UNSUPPORTED, "boson-sampling plans are not sharded");
-    pq_plan* P = new (std::nothrow) pq_plan();
+    pq_plan* P = plan_new();
     if (!P)
         return fail(PQ_ERR_NOMEM, "host allocation failed");
     int rc = plan_common_init(P, opts);
     if (rc != PQ_OK) {
-        delete P;
+        plan_delete(P);
         return rc;
     }
     P->kind = 1;
@@ -698,7 +711,7 @@ extern "C" int pq_plan_create_bs(int32_t m, const int32_t* in_occ, const int32_t
         double ft = 1.0;
         for (int i = 0; i < m; ++i) {
             if (t[i] < 0) {
-                delete P;
+                plan_delete(P);
                 return fail(PQ_ERR_ARG, "negative output occupation in pattern %lld",
                             (long long)b);
             }
@@ -706,14 +719,14 @@ extern "C" int pq_plan_create_bs(int32_t m, const int32_t* in_occ, const int32_t
             ft *= factorial_d(t[i]);
         }
         if (nt != ns) {
-            delete P;
+            plan_delete(P);
             return fail(PQ_ERR_ARG, "pattern %lld has %d photons, input has %d", (long long)b, nt,
                         ns);
         }
         // rows = output modes (t), columns = input modes (s); U[out][in]
         rc = build_item(t, in_occ, m, m, 0, m, P->items[b]);
         if (rc != PQ_OK) {
-            delete P;
+            plan_delete(P);
             return fail(rc, "pattern %lld: %s", (long long)b, g_err.c_str());
         }
         P->items[b].norm = 1.0 / (ft * fs);
@@ -722,7 +735,7 @@ extern "C" int pq_plan_create_bs(int32_t m, const int32_t* in_occ, const int32_t
     rc = schedule_and_upload(P);
     if (rc != PQ_OK) {
         free_plan_device(P);
-        delete P;
+        plan_delete(P);
         return rc;
     }
     *out = P;
@@ -735,7 +748,7 @@ extern "C" int pq_plan_destroy(pq_plan* P)
         return PQ_OK;
     cudaDeviceSynchronize();
     free_plan_device(P);
-    delete P;
+    plan_delete(P);
     return PQ_OK;
 }
 
@@ -763,6 +776,9 @@ static ExecArgs exec_args(pq_plan* P, const void* src, void* amps, double* probs
     a.partials = P->partials_d;
     a.counters = P->counters_d;
     a.err = P->err_d;
+    a.nperm = P->nperm;
+    a.nmeta = (int64_t)P->meta_h.size();
+    a.nslots = P->nslots;
     return a;
 }
 
@@ -828,6 +844,66 @@ static int run_forward(pq_plan* P, const void* src, void* amps, double* probs, c
     }
     PQ_CUDA(cudaGraphLaunch(P->graph, st));
     return PQ_OK;
+}
+
+// Read (and optionally clear) the plan's device error record; synchronous.
+static int read_device_error(pq_plan* P, int32_t* code, int64_t* task, bool clear)
+{
+    int32_t rec[2] = {0, 0};
+    *code = 0;
+    *task = 0;
+    if (!P->err_d)
+        return PQ_OK;
+    PQ_CUDA(cudaMemcpy(rec, P->err_d, sizeof(rec), cudaMemcpyDeviceToHost));
+    if (clear && (rec[0] || rec[1]))
+        PQ_CUDA(cudaMemset(P->err_d, 0, sizeof(rec)));
+    *code = rec[0];
+    *task = rec[1];
+    return PQ_OK;
+}
+
+// After the synchronous convenience path: fail loudly if a guard tripped.
+static int check_device_error(pq_plan* P)
+{
+    int32_t code = 0;
+    int64_t task = 0;
+    int rc = read_device_error(P, &code, &task, false);
+    if (rc != PQ_OK)
+        return rc;
+    if (code)
+        return fail(PQ_ERR_STATE, "kernel guard %d tripped at task %lld", code, (long long)task);
+    return PQ_OK;
+}
+
+extern "C" int pq_plan_device_error(pq_plan* P, int32_t* code, int64_t* task, int32_t clear)
+{
+    if (!P || !code || !task)
+        return fail(PQ_ERR_ARG, "null argument");
+    return read_device_error(P, code, task, clear != 0);
+}
+
+extern "C" int pq_debug_corrupt_plan(pq_plan* P, int32_t what)
+{
+    if (!P)
+        return fail(PQ_ERR_ARG, "null plan");
+    if (P->nperm == 0)
+        return fail(PQ_ERR_ARG, "empty plan");
+    if (what == 1) {
+        Task t = P->tasks_batched_h[0];
+        t.perm = (int32_t)(P->nperm + 5);
+        PQ_CUDA(cudaMemcpy(P->tasks_batched_d, &t, sizeof(t), cudaMemcpyHostToDevice));
+        t = P->tasks_plain_h[0];
+        t.perm = (int32_t)(P->nperm + 5);
+        PQ_CUDA(cudaMemcpy(P->tasks_plain_d, &t, sizeof(t), cudaMemcpyHostToDevice));
+        return PQ_OK;
+    }
+    if (what == 2) {
+        PermDesc D = P->desc_h[0];
+        D.l = P->lmax + 7;
+        PQ_CUDA(cudaMemcpy(P->desc_d, &D, sizeof(D), cudaMemcpyHostToDevice));
+        return PQ_OK;
+    }
+    return fail(PQ_ERR_ARG, "unknown corruption %d", what);
 }
 
 // Sizes of a device batch descriptor copied to the host (convenience path).
@@ -924,6 +1000,8 @@ extern "C" int pq_permanent_batched(const pq_batch* b, pq_c128* out, pq_plan* pl
         if (e != cudaSuccess)
             rc = fail(PQ_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
     }
+    if (rc == PQ_OK)
+        rc = check_device_error(P);
     pq_plan_destroy(P);
     return rc;
 }
@@ -972,6 +1050,8 @@ extern "C" int pq_bs_probs(const pq_c128* U, int32_t m, const int32_t* in_occ,
         if (e != cudaSuccess)
             rc = fail(PQ_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
     }
+    if (rc == PQ_OK)
+        rc = check_device_error(P);
     pq_plan_destroy(P);
     return rc;
 }
@@ -1080,6 +1160,7 @@ static int ensure_backward(pq_plan* P)
         const int64_t nt = it.trivial ? 1 : (it.nchunks + kWarp - 1) / kWarp;
         D.ntasks = (int32_t)nt;
         D.slot0 = 0;
+        D.part0 = 0;
         P->plain_first_bwd[p] = (int64_t)P->tasks_bwd_plain_h.size();
         const int64_t kl = (int64_t)it.k * it.l;
         gpart_off[p] = gpart;
@@ -1147,8 +1228,12 @@ static int ensure_backward(pq_plan* P)
         return rc;
     if ((rc = dev_upload(&P->grad_local_off_d, gl_off)) != PQ_OK)
         return rc;
-    PQ_CUDA(cudaMalloc((void**)&P->gpart_d, std::max<int64_t>(gpart, 1) * 2 * sizeof(double)));
-    PQ_CUDA(cudaMalloc((void**)&P->grad_local_d, std::max<int64_t>(gl, 1) * sizeof(double2)));
+    dev_free(P->gpart_d);
+    dev_free(P->grad_local_d);
+    P->gpart_d = nullptr;
+    P->grad_local_d = nullptr;
+    PQ_ALLOC(&P->gpart_d, std::max<int64_t>(gpart, 1) * 2 * sizeof(double));
+    PQ_ALLOC(&P->grad_local_d, std::max<int64_t>(gl, 1) * sizeof(double2));
     P->gpart_elems = (size_t)gpart;
     P->grad_local_elems = (size_t)gl;
     if (P->kind == 0) {
@@ -1220,6 +1305,8 @@ static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, co
     a.grad_local_off = P->grad_local_off_d;
     a.counters = P->counters_d;
     a.err = P->err_d;
+    a.nperm = P->nperm;
+    a.nmeta = (int64_t)P->meta_h.size();
     cudaError_t e;
     if (P->opts.method == PQ_METHOD_PLAIN) {
         a.tasks = P->tasks_bwd_plain_d;
@@ -1285,6 +1372,8 @@ extern "C" int pq_permanent_backward(const pq_batch* b, const pq_c128* grad_out,
             if (e != cudaSuccess)
                 rc = fail(PQ_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
         }
+        if (rc == PQ_OK)
+            rc = check_device_error(P);
         pq_plan_destroy(P);
     }
     return rc;
@@ -1326,6 +1415,8 @@ extern "C" int pq_bs_probs_backward(const pq_c128* U, int32_t m, const int32_t* 
             if (e != cudaSuccess)
                 rc = fail(PQ_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
         }
+        if (rc == PQ_OK)
+            rc = check_device_error(P);
         pq_plan_destroy(P);
     }
     return rc;
@@ -1390,7 +1481,7 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
         return PQ_OK;
     cudaStream_t st = (cudaStream_t)stream;
     double2* amps = nullptr;
-    PQ_CUDA(cudaMalloc((void**)&amps, (size_t)P->nperm * sizeof(double2)));
+    PQ_ALLOC(&amps, (size_t)P->nperm * sizeof(double2));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1448,7 +1539,7 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
     P->bwd_ready = false;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(amps);
+    dev_free(amps);
     return rc;
 }
 
@@ -1492,12 +1583,12 @@ int plan_create_occupations(int32_t m, const std::vector<int32_t>& t, const std:
                             int64_t B, pq_plan** out)
 {
     *out = nullptr;
-    pq_plan* P = new (std::nothrow) pq_plan();
+    pq_plan* P = plan_new();
     if (!P)
         return fail(PQ_ERR_NOMEM, "host allocation failed");
     int rc = plan_common_init(P, nullptr);
     if (rc != PQ_OK) {
-        delete P;
+        plan_delete(P);
         return rc;
     }
     P->kind = 2;
@@ -1506,7 +1597,7 @@ int plan_create_occupations(int32_t m, const std::vector<int32_t>& t, const std:
     for (int64_t b = 0; b < B; ++b) {
         rc = build_item(t.data() + b * m, s.data() + b * m, m, m, 0, m, P->items[b]);
         if (rc != PQ_OK) {
-            delete P;
+            plan_delete(P);
             return rc;
         }
         P->items[b].norm = 1.0;
@@ -1515,7 +1606,7 @@ int plan_create_occupations(int32_t m, const std::vector<int32_t>& t, const std:
     rc = schedule_and_upload(P);
     if (rc != PQ_OK) {
         free_plan_device(P);
-        delete P;
+        plan_delete(P);
         return rc;
     }
     *out = P;

@@ -202,6 +202,45 @@ __device__ __forceinline__ MetaView meta_view(const int32_t* pool, const PermDes
     return m;
 }
 
+// ---------------------------------------------------------------- task guards
+// The checks a task passes before any of its data is used (the error record
+// of pq_internal.h): the permanent it names, its part, the descriptor's sizes
+// against the launch's shared-memory layout (kmax rows, ld columns, jmax low
+// digits), the digit counts against the walk's limits, and the descriptor's
+// indices into the metadata pool, the partial slots and the outputs.
+// nslots < 0: the caller indexes its own slots (no slot check).  Returns 0 or
+// the error code.  The guard reads the descriptor through the L2 path into a
+// copy of its own, so the task's code loads what it needs afterwards and no
+// descriptor stays live in registers across the task.
+__device__ __forceinline__ int32_t task_guard(const Task& t, const PermDesc* desc, int64_t nperm,
+                                           int64_t nmeta, int64_t nslots, int kmax, int ld,
+                                           int jmax)
+{
+    if (t.perm < 0 || (int64_t)t.perm >= nperm)
+        return kErrTaskPerm;
+    PermDesc D = desc[t.perm];
+    if (D.k < 0 || D.l < 0 || D.k > kmax || D.l > ld)
+        return kErrDescLayout;
+    if (D.J < 0 || D.J > jmax || D.J > kMaxLowDigits || D.ndig < D.J || D.ndig > 64)
+        return kErrDescDigits;
+    if (D.meta < 0 || (int64_t)D.meta + meta_size(D.k, D.l, D.ndig) > nmeta || D.out < 0 ||
+        (int64_t)D.out >= nperm || D.ntasks < 1)
+        return kErrDescIndex;
+    if (nslots >= 0 && (D.slot0 < 0 || (int64_t)D.slot0 + D.ntasks > nslots))
+        return kErrDescIndex;
+    const int64_t q = (int64_t)t.part - D.part0;
+    if (q < 0 || q >= D.ntasks)
+        return kErrTaskPart;
+    return 0;
+}
+
+// Keep the first failure: the code, then the task's index in the list.
+__device__ __forceinline__ void record_error(int32_t* err, int32_t code, int64_t ti)
+{
+    if (atomicCAS(err, 0, code) == 0)
+        atomicExch(err + 1, (int32_t)ti);
+}
+
 // Warp-uniform state of the walk over the J low digits of a chunk.  Digit d
 // occupies bits [4d, 4d+4) of v (odometer value) and g (Gray value).
 struct LowWalk {

@@ -65,7 +65,7 @@ struct alignas(16) PermDesc {
 // n_m the number of columns with c_j >= m, so a term needs l - 1 products for
 // P(l) plus one product per extra prefix: ecnt[j] = c_j - max(c_{j+1}, 1)
 // (c_l = 0) extra copies of P(j + 1).
-inline int meta_size(int k, int l, int ndig) { return 2 * k + 3 * l + 3 * ndig; }
+__host__ __device__ inline int meta_size(int k, int l, int ndig) { return 2 * k + 3 * l + 3 * ndig; }
 
 struct alignas(8) Task {
     int32_t perm;  // permanent
@@ -87,7 +87,20 @@ struct ExecArgs {
                           // permanent (re hi, re lo, im hi, im lo); nullable
     double* partials;     // 4 doubles per task slot
     int32_t* counters;    // [0] task queue head, [1 + p] finished tasks of p
-    int32_t* err;         // device error word (0 = ok)
+    int32_t* err;         // device error record, see below
+    int64_t nperm;        // permanents of the plan (bound of Task::perm and PermDesc::out)
+    int64_t nmeta;        // entries of the metadata pool
+    int64_t nslots;       // task slots of `partials`
 };
+
+// Device error record (two int32 words, zero = no error): the kernels check
+// every task and the descriptor it names against the launch before using
+// them, skip a task that fails and keep the first failure: err[0] = one of
+// the codes below, err[1] = the index of the task in the task list.
+constexpr int32_t kErrTaskPerm = 1;     // task names a permanent outside the batch
+constexpr int32_t kErrTaskPart = 2;     // task part outside its permanent's range
+constexpr int32_t kErrDescLayout = 3;   // k or l beyond the launch's shared-memory layout
+constexpr int32_t kErrDescDigits = 4;   // digit counts beyond the walk's limits
+constexpr int32_t kErrDescIndex = 5;    // metadata, partial slots or output outside the plan's arrays
 
 }  // namespace pqi

@@ -79,7 +79,9 @@ struct BwdArgs {
     double2* grad_local;       // per permanent: oriented k x l gradient (complex)
     int64_t* grad_local_off;   // per permanent: offset of its block
     int32_t* counters;
-    int32_t* err;
+    int32_t* err;             // device error record (pq_internal.h)
+    int64_t nperm;            // permanents (bound of Task::perm)
+    int64_t nmeta;            // entries of the metadata pool
 };
 int bwd_smem_bytes_for(int kmax, int lmax, int jb, int n2);
 constexpr int kBwdMaxLowDigits = 4;  // low digits the backward workspace holds
@@ -105,6 +107,19 @@ cudaError_t clements_forward(const double* theta, const double* phi, int m, doub
                              cudaStream_t st);
 cudaError_t clements_backward(const double* theta, const double* phi, int m, const double2* U,
                               const double2* gU, double* gtheta, double* gphi, cudaStream_t st);
+
+// ---- runtime services (pq_runtime.cu)
+// Every device buffer of the library comes from dev_alloc and goes back
+// through dev_free, which count the live buffers; the test hook of
+// pq_debug_fail_allocation makes one allocation report failure.
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+// The same hook and count for the host objects the library creates (plans).
+bool host_object_alloc_ok();
+void host_object_freed();
+// Process-wide chunk length (log2) per photon number; 0 = default.
+int tune_get(int n);
+void tune_set(int n, int v);
 
 // ---- error message of the calling thread, read by pq_last_error (pq_api.cu)
 void set_last_error(const char* msg);

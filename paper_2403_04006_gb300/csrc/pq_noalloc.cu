@@ -312,6 +312,9 @@ extern "C" int pq_permanent_noalloc(const pq_c128* B, int32_t k, int32_t l,
     a.partials = partials_d;
     a.counters = counters_d;
     a.err = counters_d + 8;
+    a.nperm = 1;
+    a.nmeta = (int64_t)(sizeof(h.meta) / sizeof(h.meta[0]));
+    a.nslots = ntasks;
     int64_t want = (ntasks + wpb - 1) / wpb;
     int blocks = sms * bps;
     if (want < blocks)

@@ -47,6 +47,7 @@ struct pq_plan {
     int device = 0;
     int num_sms = 0;
     int64_t nperm = 0;
+    int64_t nslots = 0;  // partial-sum slots of the forward
     int lmax = 8;
     int kmax = 1;
     int wpb = 8;

@@ -209,13 +209,13 @@ extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_oc
     double *w_d = nullptr, *u_d = nullptr;
     int32_t *cols_d = nullptr, *drawn_d = nullptr, *err_d = nullptr;
     if (rc == PQ_OK &&
-        (cudaMalloc((void**)&mats_d, mat_elems * sizeof(double2)) != cudaSuccess ||
-         cudaMalloc((void**)&per_d, Bmax * sizeof(double2)) != cudaSuccess ||
-         cudaMalloc((void**)&w_d, nsamples * m * sizeof(double)) != cudaSuccess ||
-         cudaMalloc((void**)&u_d, nsamples * n * sizeof(double)) != cudaSuccess ||
-         cudaMalloc((void**)&cols_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
-         cudaMalloc((void**)&drawn_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
-         cudaMalloc((void**)&err_d, sizeof(int32_t)) != cudaSuccess))
+        (dev_alloc((void**)&mats_d, mat_elems * sizeof(double2)) != cudaSuccess ||
+         dev_alloc((void**)&per_d, Bmax * sizeof(double2)) != cudaSuccess ||
+         dev_alloc((void**)&w_d, nsamples * m * sizeof(double)) != cudaSuccess ||
+         dev_alloc((void**)&u_d, nsamples * n * sizeof(double)) != cudaSuccess ||
+         dev_alloc((void**)&cols_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
+         dev_alloc((void**)&drawn_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
+         dev_alloc((void**)&err_d, sizeof(int32_t)) != cudaSuccess))
         rc = report(PQ_ERR_NOMEM, "sampler workspace allocation failed");
     if (rc == PQ_OK &&
         (cudaMemcpyAsync(u_d, uniforms, nsamples * n * sizeof(double), cudaMemcpyHostToDevice,
@@ -260,13 +260,13 @@ extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_oc
         rc = report(PQ_ERR_ARG, "all weights of a sampling step are zero");
     if (rc != PQ_OK)
         cudaStreamSynchronize(st);
-    cudaFree(mats_d);
-    cudaFree(per_d);
-    cudaFree(w_d);
-    cudaFree(u_d);
-    cudaFree(cols_d);
-    cudaFree(drawn_d);
-    cudaFree(err_d);
+    dev_free(mats_d);
+    dev_free(per_d);
+    dev_free(w_d);
+    dev_free(u_d);
+    dev_free(cols_d);
+    dev_free(drawn_d);
+    dev_free(err_d);
     for (pq_plan* P : plans)
         if (P)
             pq_plan_destroy(P);

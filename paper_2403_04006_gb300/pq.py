@@ -26,6 +26,12 @@ PQ_ERR_NOMEM = -5
 PQ_ERR_STATE = -6
 PQ_METHOD_BATCHED = 0
 PQ_METHOD_PLAIN = 1
+PQ_MAX_N = 48
+PQ_DEVERR_TASK_PERM = 1
+PQ_DEVERR_TASK_PART = 2
+PQ_DEVERR_LAYOUT = 3
+PQ_DEVERR_DIGITS = 4
+PQ_DEVERR_INDEX = 5
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -75,6 +81,7 @@ _SIGNATURES = {
     "pq_plan_get_stats": (_i32, [_vp, ctypes.POINTER(pq_plan_stats)]),
     "pq_probe_fp64_peak": (_i32, [_i64, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double), _vp]),
+    "pq_probe_fp64_sweep": (_i32, [_i32, _i32, _i32, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
     "pq_permanent_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp]),
     "pq_bs_sample": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "pq_bs_probs_lossy": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp]),
@@ -86,6 +93,16 @@ _SIGNATURES = {
     "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "pq_loop_poly_factors": (_i32, [_i32, _vp]),
+    "pq_combine_partials": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
+    "pq_combine_partials_host": (_i32, [_vp, _i32, _i64, _vp, _vp]),
+    "pq_tune_table_get": (_i32, [_vp]),
+    "pq_tune_table_set": (_i32, [_vp]),
+    "pq_tune_cache_save": (_i32, [ctypes.c_char_p, ctypes.c_char_p]),
+    "pq_tune_cache_load": (_i32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(_i32)]),
+    "pq_plan_device_error": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), _i32]),
+    "pq_debug_fail_allocation": (_i32, [_i64]),
+    "pq_debug_live_allocations": (_i32, [ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "pq_debug_corrupt_plan": (_i32, [_vp, _i32]),
     "pq_last_error": (ctypes.c_char_p, []),
     "pq_version": (ctypes.c_char_p, []),
 }
@@ -205,6 +222,15 @@ def pq_probe_fp64_peak(iters: int, stream=None) -> tuple[float, float]:
     return f.value, ms.value
 
 
+def pq_probe_fp64_sweep(op: int, warps_per_sm: int, chains: int, iters: int,
+                        stream=None) -> float:
+    """Lane operations per second per SM of op (0 DFMA, 1 DADD, 2 DMUL)."""
+    r = ctypes.c_double()
+    _check(load_library().pq_probe_fp64_sweep(op, warps_per_sm, chains, iters, ctypes.byref(r),
+                                              stream), "pq_probe_fp64_sweep")
+    return r.value
+
+
 def pq_permanent_noalloc(B_ptr, k: int, l: int, row_mult: np.ndarray, col_mult: np.ndarray,
                          out_ptr, stream):
     """Permanent of one base matrix with no device allocation (static device
@@ -293,6 +319,79 @@ def pq_bs_probs_lossy(V_ptr, eta_ptr, W_ptr, m: int, input_occ: np.ndarray,
     t = np.ascontiguousarray(output_occ, dtype=np.int32).reshape(-1, m)
     _check(load_library().pq_bs_probs_lossy(V_ptr, eta_ptr, W_ptr, m, s.ctypes.data, t.ctypes.data,
                                             t.shape[0], probs_ptr, stream), "pq_bs_probs_lossy")
+
+
+def pq_combine_partials(parts_ptr, nshards: int, batch: int, n_ptr, out_ptr, stream):
+    """Device pointers: parts (nshards x batch x 4 doubles), n (int32), out (complex)."""
+    _check(load_library().pq_combine_partials(parts_ptr, nshards, batch, n_ptr, out_ptr, stream),
+           "pq_combine_partials")
+
+
+def pq_combine_partials_host(parts: np.ndarray, n: np.ndarray) -> np.ndarray:
+    """Host arrays: parts (nshards, batch, 4) float64, n (batch,) int; returns
+    the complex permanents."""
+    p = np.ascontiguousarray(parts, dtype=np.float64)
+    if p.ndim != 3 or p.shape[2] != 4:
+        raise ValueError("parts must have shape (nshards, batch, 4)")
+    nn = np.ascontiguousarray(n, dtype=np.int32)
+    batch = p.shape[1]
+    if nn.shape != (batch,):
+        raise ValueError("n must have one entry per permanent")
+    out = np.zeros(batch, dtype=np.complex128)
+    _check(load_library().pq_combine_partials_host(p.ctypes.data if p.size else None, p.shape[0],
+                                                   batch, nn.ctypes.data if nn.size else None,
+                                                   out.ctypes.data if out.size else None),
+           "pq_combine_partials_host")
+    return out
+
+
+def pq_tune_table_get() -> np.ndarray:
+    t = np.zeros(PQ_MAX_N + 1, dtype=np.int32)
+    _check(load_library().pq_tune_table_get(t.ctypes.data), "pq_tune_table_get")
+    return t
+
+
+def pq_tune_table_set(table) -> None:
+    t = np.ascontiguousarray(table, dtype=np.int32)
+    if t.shape != (PQ_MAX_N + 1,):
+        raise ValueError(f"the tuning table has {PQ_MAX_N + 1} entries")
+    _check(load_library().pq_tune_table_set(t.ctypes.data), "pq_tune_table_set")
+
+
+def pq_tune_cache_save(path: str, device_key: str | None = None) -> None:
+    _check(load_library().pq_tune_cache_save(os.fsencode(path),
+                                             None if device_key is None else device_key.encode()),
+           "pq_tune_cache_save")
+
+
+def pq_tune_cache_load(path: str, device_key: str | None = None) -> bool:
+    found = _i32()
+    _check(load_library().pq_tune_cache_load(os.fsencode(path),
+                                             None if device_key is None else device_key.encode(),
+                                             ctypes.byref(found)), "pq_tune_cache_load")
+    return bool(found.value)
+
+
+def pq_plan_device_error(plan: int, clear: bool = False) -> tuple[int, int]:
+    code, task = _i32(), _i64()
+    _check(load_library().pq_plan_device_error(plan, ctypes.byref(code), ctypes.byref(task),
+                                               1 if clear else 0), "pq_plan_device_error")
+    return code.value, task.value
+
+
+def pq_debug_fail_allocation(after: int) -> None:
+    _check(load_library().pq_debug_fail_allocation(after), "pq_debug_fail_allocation")
+
+
+def pq_debug_live_allocations() -> tuple[int, int]:
+    d, h = _i64(), _i64()
+    _check(load_library().pq_debug_live_allocations(ctypes.byref(d), ctypes.byref(h)),
+           "pq_debug_live_allocations")
+    return d.value, h.value
+
+
+def pq_debug_corrupt_plan(plan: int, what: int) -> None:
+    _check(load_library().pq_debug_corrupt_plan(plan, what), "pq_debug_corrupt_plan")
 
 
 def pq_version() -> str:

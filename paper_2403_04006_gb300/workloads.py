@@ -198,11 +198,18 @@ def _parts(n: int, rng) -> list[int]:
     return out
 
 
-def ragged(count: int = 65536, nmin: int = 4, nmax: int = 20) -> PermBatch:
+def ragged(count: int = 65536, nmin: int = 4, nmax: int = 20, block: int = 0,
+           sizes_only: bool = False) -> PermBatch:
     """Ragged batch: n ~ U{nmin..nmax}; row and column multiplicities drawn
     independently as ``_parts``; distinct row modes and distinct column modes
-    drawn from 0..2n-1 of the item's own Haar 2n x 2n unitary."""
-    rng = rng_for(4)
+    drawn from 0..2n-1 of the item's own Haar 2n x 2n unitary.
+
+    ``block`` b > 0 draws another batch of the same recipe from seed streams
+    of its own (sizes from stream 1000 b, unitaries of size 2n from stream
+    1000 b + n): block r is rank r's part of a batch of several blocks split
+    over ranks.  Block 0 is the benchmark batch.  ``sizes_only`` skips the
+    unitaries (all base matrices zero): the sizes and multiplicities alone."""
+    rng = rng_for(4) if block == 0 else rng_for(4, 1000 * block)
     ns = rng.integers(nmin, nmax + 1, size=count)
     rows_l, cols_l, rs, cs = [], [], [], []
     for b in range(count):
@@ -214,11 +221,14 @@ def ragged(count: int = 65536, nmin: int = 4, nmax: int = 20) -> PermBatch:
         rs.append(r)
         cs.append(c)
     items = [None] * count
+    if sizes_only:
+        return pack_batch([(np.zeros((len(rs[b]), len(cs[b])), dtype=np.complex128), rs[b], cs[b])
+                           for b in range(count)])
     for n in range(nmin, nmax + 1):
         idx = np.nonzero(ns == n)[0]
         if idx.size == 0:
             continue
-        Us = haar_unitaries(idx.size, 2 * n, rng_for(4, n))
+        Us = haar_unitaries(idx.size, 2 * n, rng_for(4, n if block == 0 else 1000 * block + n))
         for q, b in enumerate(idx):
             B = Us[q][np.ix_(rows_l[b], cols_l[b])]
             items[b] = (B, rs[b], cs[b])

@@ -1,7 +1,8 @@
-"""The bench's multi-rank bookkeeping on CPU with gloo (world size 2): every
-rank runs its own batch (weak scaling, no data-path collective); the timed
-region is closed by a barrier, the time is the maximum over ranks and the
-throughput counts the units of all ranks."""
+"""The bench's multi-rank bookkeeping on CPU with gloo (world size 2): rank r
+evaluates block r of the job's batch (weak scaling, no data-path
+collective); the timed region is closed by a barrier, the time is the
+maximum over ranks and the throughput counts the units of all ranks' blocks.
+Both arms of the bench describe the same job in the same config object."""
 import os
 import socket
 import sys
@@ -33,7 +34,11 @@ def _worker(rank, world, port, q):
     bench.barrier()
     slowest = bench.max_over_ranks(my_seconds)
     rate = bench.whole_job_rate(1000.0, w, slowest)
-    q.put((rank, slowest, rate))
+    from paper_2403_04006_gb300 import workloads as W
+    blk = W.ragged(count=256, block=rank, sizes_only=True)  # this rank's block
+    terms = bench.glynn_terms(blk, range(blk.batch))
+    job = bench.sum_over_ranks(terms)
+    q.put((rank, slowest, rate, terms, job))
     import torch.distributed as dist
     dist.destroy_process_group()
 
@@ -49,9 +54,12 @@ def test_max_over_ranks_and_weak_scaling_rate():
         p.join(timeout=120)
         assert p.exitcode == 0
     got = sorted(q.get(timeout=10) for _ in range(2))
-    for rank, slowest, rate in got:
+    block_terms = [g[3] for g in got]
+    assert block_terms[0] != block_terms[1]  # two different blocks
+    for rank, slowest, rate, terms, job in got:
         assert slowest == 2.0          # max over ranks
         assert rate == 1000.0 * 2 / 2.0  # all ranks' units / slowest time
+        assert job == sum(block_terms)   # the job's terms: every rank's block
 
 
 def test_single_process_helpers():
@@ -59,3 +67,12 @@ def test_single_process_helpers():
     import bench
     assert bench.whole_job_rate(10.0, 1, 2.0) == 5.0
     assert bench.max_over_ranks(3.0) == 3.0  # no process group: identity
+    assert bench.sum_over_ranks(3.0) == 3.0
+
+
+def test_both_arms_describe_the_same_job():
+    sys.path.insert(0, ROOT)
+    import bench
+    a = bench.bench_config(bench.WORKLOAD, 65536, 176370045, 1)
+    b = bench.bench_config(bench.WORKLOAD, 65536, 176370045, 1)
+    assert a == b and set(a) == {"workload", "permanents", "terms", "parallelism", "l2"}

@@ -1,7 +1,8 @@
 """Host side of a permanent split over ranks (the exchange step of one large
-permanent spread across GPUs): the double-double combination of the shards'
-partial sums, pinned by exact rational arithmetic, and the all_gather of the
-partials across two gloo ranks on CPU."""
+permanent spread across GPUs): the library's double-double combination of
+the shards' partial sums (pq_combine_partials_host, the host twin of the
+device kernel pq_combine_partials), pinned by exact rational arithmetic, and
+the all_gather of the partials across two gloo ranks on CPU."""
 import os
 import socket
 import sys
@@ -44,6 +45,12 @@ def make_parts(rng, nshards, batch):
     parts[-1][0, 0], parts[-1][0, 1] = -1.0e6, 4.0e-11
     for p in parts[1:-1]:
         p[0, :2] = 0.0
+    if nshards >= 3:
+        # item 2 (imaginary part): 1 + 2^-60 - 1, whose value is only the
+        # rounding error of the first high-part addition
+        for p in parts:
+            p[2, 2:] = 0.0
+        parts[0][2, 2], parts[1][2, 2], parts[2][2, 2] = 1.0, 2.0 ** -60, -1.0
     return parts
 
 
@@ -66,6 +73,8 @@ def test_combination_is_the_exact_sum_rounded(nshards):
     if nshards > 1:
         # the cancelling item: a plain double sum would lose it entirely
         assert abs(got[0].real - 7.0e-11) <= 1e-24
+    if nshards >= 3:
+        assert got[2].imag == np.ldexp(2.0 ** -60, 1 - int(n[2]))
 
 
 def _free_port():
@@ -115,4 +124,18 @@ def test_gather_over_two_gloo_ranks():
 def test_single_process_gather_is_local():
     t = torch.arange(8, dtype=torch.float64).reshape(2, 4)
     g = api.gather_partials(t)
-    assert len(g) == 1 and np.array_equal(g[0], t.numpy())
+    assert len(g) == 1 and np.array_equal(g[0].numpy(), t.numpy())
+
+
+def test_combine_argument_errors():
+    from paper_2403_04006_gb300 import pq
+    parts = np.zeros((2, 3, 4))
+    with pytest.raises(pq.PQError) as e:
+        pq.pq_combine_partials_host(parts, np.array([1, 2, 49]))  # n above PQ_MAX_N
+    assert e.value.code == pq.PQ_ERR_ARG
+    with pytest.raises(ValueError):
+        pq.pq_combine_partials_host(parts, np.array([1, 2]))
+    assert pq.pq_combine_partials_host(np.zeros((1, 0, 4)), np.zeros(0)).shape == (0,)
+    one = np.zeros((3, 1, 4))
+    one[1, 0, 0] = 1.0  # n = 0: the shard that held the permanent contributes 1
+    assert pq.pq_combine_partials_host(one, np.array([0]))[0] == 1.0
