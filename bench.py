@@ -27,8 +27,9 @@ rank's time.
 Profiling cases (``--workload``; same JSON line, smaller or different work,
 never the benchmark figure): ``ragged4096`` and ``single30`` run the same
 forward on a 4096-permanent batch of the recipe or the n = 30 permanent;
-``ragged4096-backward`` times the backward (one launch per product-column
-class and the scatter) on the 4096-permanent batch; ``hafnian-2x`` and
+``ragged-backward`` and ``ragged4096-backward`` time the backward (one launch
+per product-column class and the scatter) on the benchmark batch or the
+4096-permanent batch; ``hafnian-2x`` and
 ``loop-hafnian-2x`` time the repeated (loop) hafnian of a k x k GBS matrix
 with every index repeated twice (``--k``); ``fp64-sweep`` measures the FP64
 pipe (DFMA, DADD, DMUL) against resident warps per SM and independent chains
@@ -189,7 +190,8 @@ def profiled_traffic():
     return float(b.group(1))
 
 
-PROFILE_CASES = ("ragged4096-backward", "hafnian-2x", "loop-hafnian-2x", "fp64-sweep")
+PROFILE_CASES = ("ragged-backward", "ragged4096-backward", "hafnian-2x", "loop-hafnian-2x",
+                 "fp64-sweep")
 
 
 def load_workload(name: str, block: int = 0):
@@ -201,6 +203,8 @@ def load_workload(name: str, block: int = 0):
         if block == 0:
             return W.ragged(), WORKLOAD
         return W.ragged(block=block), WORKLOAD + f", block {block} (own seed streams)"
+    if name == "ragged-backward":
+        return W.ragged(), WORKLOAD + ", backward (profiling case)"
     if name in ("ragged4096", "ragged4096-backward"):
         return W.ragged(count=4096), "ragged recipe with 4096 permanents (profiling case)"
     if name == "single30":
@@ -624,7 +628,7 @@ def bench_case(args, dev):
         return
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     extra = {}
-    if args.workload == "ragged4096-backward":
+    if args.workload in ("ragged-backward", "ragged4096-backward"):
         pb, desc = load_workload(args.workload)
         db = api.DeviceBatch(pb, dev)
         plan = api.Plan.for_batch(pb, method="batched")
@@ -633,7 +637,8 @@ def bench_case(args, dev):
         def op():
             api.permanent_backward(db, gout, plan, stream=stream)
         terms_of = lambda: plan.stats()["terms"]  # noqa: E731
-        desc = desc.replace("(profiling case)", "backward (profiling case)")
+        if args.workload == "ragged4096-backward":
+            desc = desc.replace("(profiling case)", "backward (profiling case)")
     else:
         loop = args.workload.startswith("loop")
         B, r, g = W.paper_repeated_hafnian(args.k, loop=loop)
@@ -664,7 +669,7 @@ def bench_case(args, dev):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     torch.cuda.nvtx.range_pop()
-    if args.workload == "ragged4096-backward":
+    if args.workload in ("ragged-backward", "ragged4096-backward"):
         st = plan.stats()
         extra = {"fp64_instr_backward": st["fp64_instr_backward"],
                  "launches": st["launches_backward"]}

@@ -90,7 +90,12 @@ __device__ __forceinline__ void acc_scaled(double2* a, double s, double2 q)
 }
 
 // A_j += ws * Q_j for this lane's column sums.  All pointers are lane-offset
-// with stride kLS.  n2 = number of leading columns with c_j >= 2.
+// with stride kLS.  n2 = number of leading columns with c_j >= 2, for which
+// PW_j = c_j S_j^{c_j - 1} (the derivative of the column power) and FULL_j =
+// S_j^{c_j} are formed first.  The prefixes P_j = prod_{j' < j} S_{j'}^{c_{j'}}
+// are stored; the suffix sw = ws prod_{j' > j} S_{j'}^{c_{j'}} carries the
+// term's weight, so that every column's accumulation A_j += P_j sw (times PW_j
+// for a repeated column) is one fused complex multiply-add.
 __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* PW, double2* FULL,
                                          double2* A, int l, int n2, const int32_t* cm, double ws)
 {
@@ -114,8 +119,9 @@ __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* 
 #pragma unroll 1
         for (int e = 2; e < cm[j]; ++e)
             pw = cmul(pw, s);
-        PW[j * kLS] = pw;
         FULL[j * kLS] = cmul(pw, s);
+        const double c = (double)cm[j];
+        PW[j * kLS] = make_double2(__dmul_rn(c, pw.x), __dmul_rn(c, pw.y));
     }
     // prefix P_j = prod_{j' < j} S_{j'}^{c_{j'}}, j = 1 .. l-1
     double2 run = (n2 > 0) ? FULL[0] : S[0];
@@ -132,41 +138,46 @@ __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* 
         P[(j + 1) * kLS] = run;
     }
     // suffix pass, last column first
-    double2 sf;
+    double2 sw;
     {
         const int j = l - 1;
         double2 q = P[j * kLS];
+        double2 f;
         if (j < n2) {
             q = cmul(q, PW[j * kLS]);
-            acc_scaled(A + j * kLS, ws * (double)cm[j], q);
-            sf = FULL[j * kLS];
+            f = FULL[j * kLS];
         } else {
-            acc_scaled(A + j * kLS, ws, q);
-            sf = S[j * kLS];
+            f = S[j * kLS];
         }
+        acc_scaled(A + j * kLS, ws, q);
+        sw = make_double2(__dmul_rn(ws, f.x), __dmul_rn(ws, f.y));
     }
     // columns l-2 .. 1 with c_j = 1
 #pragma unroll 1
     for (int j = l - 2; j >= 1 && j >= n2; --j) {
-        const double2 q = cmul(P[j * kLS], sf);
-        acc_scaled(A + j * kLS, ws, q);
-        sf = cmul(sf, S[j * kLS]);
+        double2 av = A[j * kLS];
+        cfma_acc<false>(av, P[j * kLS], sw);
+        A[j * kLS] = av;
+        sw = cmul(sw, S[j * kLS]);
     }
     // columns min(n2, l-1) - 1 .. 1 with c_j >= 2
 #pragma unroll 1
     for (int j = (n2 < l - 1 ? n2 : l - 1) - 1; j >= 1; --j) {
-        double2 q = cmul(P[j * kLS], sf);
-        q = cmul(q, PW[j * kLS]);
-        acc_scaled(A + j * kLS, ws * (double)cm[j], q);
-        sf = cmul(sf, FULL[j * kLS]);
+        const double2 q = cmul(P[j * kLS], sw);
+        double2 av = A[j * kLS];
+        cfma_acc<false>(av, q, PW[j * kLS]);
+        A[j * kLS] = av;
+        sw = cmul(sw, FULL[j * kLS]);
     }
     // column 0: Q_0 = c_0 S_0^{c_0 - 1} * prod_{j > 0}
+    double2 av = A[0];
     if (n2 > 0) {
-        const double2 q = cmul(sf, PW[0]);
-        acc_scaled(A, ws * (double)cm[0], q);
+        cfma_acc<false>(av, sw, PW[0]);
     } else {
-        acc_scaled(A, ws, sf);
+        av.x = __dadd_rn(av.x, sw.x);
+        av.y = __dadd_rn(av.y, sw.y);
     }
+    A[0] = av;
 }
 
 __device__ void bwd_stage(const BwdArgs& a, const PermDesc& D, const MetaView& mv, BwdSmem& sm,
@@ -485,31 +496,49 @@ __global__ void scatter_batch_kernel(const PermDesc* desc, const int32_t* meta,
     }
 }
 
-// Boson sampling: grad_U[a][c] = sum over patterns (in order) of the entry of
-// that pattern's gradient that U[a][c] became.  pos[p][2m] maps output mode a
-// and input mode c to the oriented (row, column) indices of pattern p's base
+// Boson sampling: grad_U[a][c] = sum over patterns of the entry of that
+// pattern's gradient that U[a][c] became.  pos[p][2m] maps output mode a and
+// input mode c to the oriented (row, column) indices of pattern p's base
 // matrix: pos[p][a] = row of a, pos[p][m + c] = column of c, -1 if absent
 // (for a pattern whose summed side is its input modes the roles swap in the
 // planner, which writes the map accordingly).
-__global__ void scatter_bs_kernel(const PermDesc* desc, int64_t nperm, int m, const int32_t* pos,
-                                  const double2* gl, const int64_t* gl_off, double2* gU)
+//
+// One warp per entry (a, c): lane q adds the patterns [q B / 32, (q + 1) B / 32)
+// in order, then a fixed shuffle tree adds the 32 lane sums, so the result
+// is the same on every run and no floating-point atomics are needed.  The
+// loads of one pattern (map, descriptor, gradient block) are independent of
+// the next pattern's, so a lane keeps several in flight.
+__global__ void __launch_bounds__(256) scatter_bs_kernel(const PermDesc* desc, int64_t nperm,
+                                                         int m, const int32_t* pos,
+                                                         const double2* gl, const int64_t* gl_off,
+                                                         double2* gU)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
-        const int ar = e / m, ac = e - ar * m;  // U row (output mode), column (input mode)
-        double gx = 0.0, gy = 0.0;
-        for (int64_t p = 0; p < nperm; ++p) {
-            const int32_t* pp = pos + p * 2 * (int64_t)m;
-            const int io = pp[ar], jo = pp[m + ac];
-            if (io < 0 || jo < 0)
-                continue;
-            const int l = desc[p].l;
-            const bool tr = desc[p].si == 1 && m > 1;  // summed side = input modes
-            const double2 v = gl[gl_off[p] + (tr ? (int64_t)jo * l + io : (int64_t)io * l + jo)];
-            gx += v.x;
-            gy += v.y;
-        }
-        gU[e] = make_double2(gx, gy);
+    const int lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (e >= (int64_t)m * m)
+        return;  // e is the same for the whole warp
+    const int ar = (int)(e / m), ac = (int)(e - (int64_t)ar * m);  // U row (output), column (input)
+    const int64_t p0 = nperm * lane / kWarp, p1 = nperm * (lane + 1) / kWarp;
+    double gx = 0.0, gy = 0.0;
+#pragma unroll 4
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t* pp = pos + p * 2 * (int64_t)m;
+        const int io = pp[ar], jo = pp[m + ac];
+        if (io < 0 || jo < 0)
+            continue;
+        const int l = desc[p].l;
+        const bool tr = desc[p].si == 1 && m > 1;  // summed side = input modes
+        const double2 v = gl[gl_off[p] + (tr ? (int64_t)jo * l + io : (int64_t)io * l + jo)];
+        gx += v.x;
+        gy += v.y;
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gx += __shfl_down_sync(0xffffffffu, gx, off);
+        gy += __shfl_down_sync(0xffffffffu, gy, off);
+    }
+    if (lane == 0)
+        gU[e] = make_double2(gx, gy);
 }
 
 // ---------------------------------------------------------------- host side
@@ -572,10 +601,10 @@ cudaError_t scatter_grad_bs(const PermDesc* desc, const int32_t* pos, int64_t np
                             const double2* grad_local, const int64_t* grad_local_off,
                             double2* grad_U, cudaStream_t st)
 {
-    const int threads = 64;
-    const int blocks = (m * m + threads - 1) / threads;
-    scatter_bs_kernel<<<blocks, threads, 0, st>>>(desc, nperm, m, pos, grad_local, grad_local_off,
-                                                  grad_U);
+    const int warps_per_block = 8;  // one warp per entry of grad_U
+    const int blocks = (m * m + warps_per_block - 1) / warps_per_block;
+    scatter_bs_kernel<<<blocks, 32 * warps_per_block, 0, st>>>(desc, nperm, m, pos, grad_local,
+                                                               grad_local_off, grad_U);
     return cudaGetLastError();
 }
 

@@ -90,12 +90,13 @@ __device__ void stage_perm(const ExecArgs& a, const PermDesc& D, const MetaView&
     __syncwarp();
 }
 
-// One Glynn term: acc +-= w * prod_j S_j^{c_j} (S = this lane's column sums,
+// One Glynn term: acc +-= prod_j S_j^{c_j} (S = this lane's column sums,
 // stride 32).  unit: every c_j = 1; jf: first column with an extra prefix.
+// The low-digit weight is applied by the caller, once per run of terms that
+// share it.
 template <bool NEG>
 __device__ __forceinline__ void glynn_term(const double2* S, int l, bool unit, int jf,
-                                           const int32_t* ecnt, bool weighted, double w,
-                                           double2& acc)
+                                           const int32_t* ecnt, double2& acc)
 {
     if (unit) {
         if (l == 1) {  // n = 1: the product is S_0 itself
@@ -107,10 +108,6 @@ __device__ __forceinline__ void glynn_term(const double2* S, int l, bool unit, i
 #pragma unroll 1
         for (int j = 1; j < l - 1; ++j)
             p = cmul(p, S[j * 32]);
-        if (weighted) {
-            p.x = __dmul_rn(p.x, w);
-            p.y = __dmul_rn(p.y, w);
-        }
         cfma_acc<NEG>(acc, p, S[(l - 1) * 32]);
         return;
     }
@@ -130,16 +127,13 @@ __device__ __forceinline__ void glynn_term(const double2* S, int l, bool unit, i
         for (int e = 0; e < ecnt[j]; ++e)
             ex = cmul(ex, pre);
     }
-    if (weighted) {
-        ex.x = __dmul_rn(ex.x, w);
-        ex.y = __dmul_rn(ex.y, w);
-    }
     cfma_acc<NEG>(acc, pre, ex);
 }
 
 // One Gray step of the warp-uniform low walk: every lane's S += -+2 b_row.
-__device__ __forceinline__ void glynn_step(LowWalk& wk, const WarpSmem& sm, double2* S, int l,
-                                           int J, bool weighted, double& wlow)
+// Returns true when the changed digit has radix > 2, i.e. when the low-digit
+// weight prod_d C(top_d, g_d) changes (a radix-2 digit has weight C(1, g) = 1).
+__device__ __forceinline__ bool glynn_step(LowWalk& wk, const WarpSmem& sm, double2* S, int l)
 {
     int up;
     const int d = low_step(wk, up);
@@ -153,8 +147,18 @@ __device__ __forceinline__ void glynn_step(LowWalk& wk, const WarpSmem& sm, doub
         s.y = __fma_rn(delta, b.y, s.y);
         S[j * 32] = s;
     }
-    if (weighted && ((wk.radm1 >> (4 * d)) & 15u) > 1u)
-        wlow = (double)low_weight(wk, J);
+    return ((wk.radm1 >> (4 * d)) & 15u) > 1u;
+}
+
+// A run of equally weighted terms ends: run += wlow * acc, and the walk's new
+// weight becomes wlow.
+__device__ __forceinline__ void reweight(const LowWalk& wk, int J, double& wlow, double2& acc,
+                                         double2& run)
+{
+    run.x = __fma_rn(wlow, acc.x, run.x);
+    run.y = __fma_rn(wlow, acc.y, run.y);
+    acc = make_double2(0.0, 0.0);
+    wlow = (double)low_weight(wk, J);
 }
 
 // Write per = 2^{-(n-1)} * sum, and |per|^2 * norm; a sharded plan writes
@@ -252,27 +256,44 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
         const bool weighted = D.weighted != 0;
         const bool unit = D.jf < 0;
         const int jf = D.jf;
+        // acc: the terms since the weight last changed (unweighted); run: the
+        // weighted sum since the last fold; every 32 terms run (or, for an
+        // unweighted permanent, acc) is folded into the double-double rh/rl,
+        // ih/il.  The weight changes only when a digit of radix > 2 moves, so
+        // it costs 2 DFMA per change instead of 2 DMUL per term.
         double wlow = 1.0;
-        double2 acc = make_double2(0.0, 0.0);
+        double2 acc = make_double2(0.0, 0.0), run = make_double2(0.0, 0.0);
         double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
         const int64_t L = D.L;
         int64_t s = 0;
         int blk = 0;
 #pragma unroll 1
         while (s < L) {
-            glynn_term<false>(S, l, unit, jf, sm.ecnt, weighted, wlow, acc);
+            glynn_term<false>(S, l, unit, jf, sm.ecnt, acc);
             if (++s < L) {
-                glynn_step(wk, sm, S, l, J, weighted, wlow);
-                glynn_term<true>(S, l, unit, jf, sm.ecnt, weighted, wlow, acc);
-                if (++s < L)
-                    glynn_step(wk, sm, S, l, J, weighted, wlow);
+                if (glynn_step(wk, sm, S, l) && weighted)
+                    reweight(wk, J, wlow, acc, run);
+                glynn_term<true>(S, l, unit, jf, sm.ecnt, acc);
+                if (++s < L && glynn_step(wk, sm, S, l) && weighted)
+                    reweight(wk, J, wlow, acc, run);
             }
-            if (++blk == 8) {
+            if (++blk == 16) {
                 blk = 0;
+                if (weighted) {
+                    run.x = __fma_rn(wlow, acc.x, run.x);
+                    run.y = __fma_rn(wlow, acc.y, run.y);
+                    acc = run;
+                    run = make_double2(0.0, 0.0);
+                }
                 dd_acc(rh, rl, acc.x);
                 dd_acc(ih, il, acc.y);
                 acc = make_double2(0.0, 0.0);
             }
+        }
+        if (weighted) {
+            run.x = __fma_rn(wlow, acc.x, run.x);
+            run.y = __fma_rn(wlow, acc.y, run.y);
+            acc = run;
         }
         dd_acc(rh, rl, acc.x);
         dd_acc(ih, il, acc.y);

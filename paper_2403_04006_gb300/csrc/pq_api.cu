@@ -198,6 +198,18 @@ static int build_item(const int32_t* r, const int32_t* c, int k0, int l0, int64_
     return PQ_OK;
 }
 
+// Share of the Gray steps of a chunk (the lowest j digits, ascending radix)
+// after which the low-digit weight prod_d C(top_d, g_d) changes: only digits
+// of radix > 2 change it, and the a leading radix-2 digits take all but
+// 2^-a of the steps.  Zero when every low digit has radix 2.
+static double weight_change_rate(const std::vector<int32_t>& drad, int j)
+{
+    int a = 0;
+    while (a < j && drad[a] == 2)
+        ++a;
+    return a == j ? 0.0 : std::ldexp(1.0, -a);
+}
+
 // Cut the item's code into chunks of the lowest digits: the longest prefix of
 // digits whose radix product stays within the target length.
 static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
@@ -232,12 +244,10 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
             cmax = std::max(cmax, c);
         const int nd = (int)it.drad.size();
         auto cost_of = [&](int j, int64_t lj) {
-            bool w = false;
-            for (int d = 0; d < j; ++d)
-                w = w || it.drad[d] > 2;
             const double products = (cmax == 1) ? (it.l - 2) : (it.l + cmax - 3);
-            const double ppt = 2.0 * it.l + 4.0 * std::max(products, 0.0) + 4.0 + (w ? 2.0 : 0.0);
-            const double ovh = (nd - j) * (2.0 * it.l + 2.0) + 120.0 + 2.0 * it.k;
+            const double ppt = 2.0 * it.l + 4.0 * std::max(products, 0.0) + 4.0 +
+                               2.0 * weight_change_rate(it.drad, j) + 10.0 / 32.0;
+            const double ovh = (nd - j) * (2.0 * it.l + 2.0) + 84.0 + 2.0 * it.k;
             const int64_t tasks = (it.T / lj + kWarp - 1) / kWarp;
             return tasks * ((double)lj * ppt + ovh);
         };
@@ -279,8 +289,8 @@ static double fwd_flops_per_term(const ItemPlan& it)
 }
 
 // FP64 instructions of one term in glynn_fwd.cu: Gray step 2l; products of
-// P(l) and the extra prefixes, 4 each; fused accumulation 4; weight 2; the
-// double-double fold, 14 every 16 terms.
+// P(l) and the extra prefixes, 4 each; fused accumulation 4; 2 DFMA per
+// change of the low-digit weight; the double-double fold, 10 every 32 terms.
 static double fwd_instr_per_term(const ItemPlan& it)
 {
     if (it.n == 1)
@@ -289,7 +299,8 @@ static double fwd_instr_per_term(const ItemPlan& it)
     for (int c : it.cmul)
         cmax = std::max(cmax, c);
     const double products = (cmax == 1) ? (it.l - 2) : (it.l + cmax - 3);
-    return 2.0 * it.l + 4.0 * products + 4.0 + (it.weighted ? 2.0 : 0.0) + 14.0 / 16.0;
+    return 2.0 * it.l + 4.0 * products + 4.0 + 2.0 * weight_change_rate(it.drad, it.J) +
+           10.0 / 32.0;
 }
 
 static double bwd_flops_per_term(const ItemPlan& it)
@@ -298,9 +309,10 @@ static double bwd_flops_per_term(const ItemPlan& it)
 }
 
 // FP64 instructions of one backward term in glynn_bwd.cu: column-sum and
-// correction updates 4l; prefixes 4(l - 2); per middle column the product of
-// prefix and suffix, its accumulation and the suffix update, 10; the end
-// columns 4; per repeated column its powers and scaling.
+// correction updates 4l; prefixes 4(l - 2); per middle column the fused
+// accumulation of prefix times weighted suffix and the suffix update, 8; the
+// end columns and the weighted suffix's start 6; per repeated column its
+// powers, the scaled derivative and one more product, 4(c - 1) + 6.
 static double bwd_instr_per_term(const ItemPlan& it)
 {
     if (it.n == 1)
@@ -309,9 +321,8 @@ static double bwd_instr_per_term(const ItemPlan& it)
     double rep = 0.0;
     for (int c : it.cmul)
         if (c >= 2)
-            rep += 4.0 * (c - 1) + 5.0;
-    return 4.0 * l + 4.0 * std::max(l - 2, 0) + 10.0 * std::max(l - 2, 0) + 4.0 + rep +
-           (it.weighted ? 1.0 : 0.0);
+            rep += 4.0 * (c - 1) + 6.0;
+    return 4.0 * l + 4.0 * std::max(l - 2, 0) + 8.0 * std::max(l - 2, 0) + 6.0 + rep;
 }
 
 static int default_log2_for(const pq_plan* P, const ItemPlan& it)
@@ -491,13 +502,13 @@ static int schedule_and_upload(pq_plan* P)
             flops_b += (double)tt * bwd_flops_per_term(it);
             // per task, every lane: L terms, the chunk start ((ndig - J) row
             // updates of 2l), the chunk's fold and scaling (28) and the lane
-            // tree (92); per permanent with several tasks, the partials'
-            // double-double sum (20 per task and lane) and one more tree
+            // tree (56); per permanent with several tasks, the partials'
+            // double-double sum (14 per task and lane) and one more tree
             const double lane = (double)it.L * fwd_instr_per_term(it) +
-                                2.0 * it.l * (double)((int)it.drow.size() - it.J) + 28.0 + 92.0;
+                                2.0 * it.l * (double)((int)it.drow.size() - it.J) + 28.0 + 56.0;
             instr_fx += (double)nt * 32.0 * lane;
             if (nt > 1)
-                instr_fx += 32.0 * (20.0 * (double)((nt + kWarp - 1) / kWarp) + 92.0);
+                instr_fx += 32.0 * (14.0 * (double)((nt + kWarp - 1) / kWarp) + 56.0);
         }
         if (slot < 0)
             return fail(PQ_ERR_UNSUPPORTED, "too many tasks");
@@ -1131,7 +1142,7 @@ static int ensure_backward(pq_plan* P)
             int wpb = 0, bps = 0;
             launch_geometry_max(bwd_regs_per_thread(C.ld), per_warp, 8, wpb, bps);
             const double warps = std::min(8.0, (double)(wpb * bps)) / 8.0;
-            const double per_term = 18.0 * C.ld + 8.0;
+            const double per_term = 16.0 * C.ld - 10.0;
             const double start = std::max(0.0, nbar - J) * 2.0 * C.ld / (double)(1 << J);
             const double score = warps * per_term / (per_term + start);
             if (score > best) {
