@@ -39,25 +39,38 @@ constexpr int kLS = 33;
 
 // Per-warp shared memory: ld = product-column bound, jb = low digits of the
 // plan's chunks, n2 = repeated product columns at most (powers are kept only
-// for those).
+// for those).  Layout: base matrix M (kmax x ld), base column sums (ld), the
+// lanes' accumulators A (ld x kLS) and corrections C (jb x ld x kLS), then a
+// region that the walk uses for the column sums S, prefixes P and powers PW,
+// FULL, and that the end-of-task contraction reuses for the lanes' row
+// multipliers X (kmax x kLS doubles) and the correction sums V (jb x ld),
+// then the weights wh (32) and small integer arrays.
+__host__ __device__ inline long bwd_walk_region_bytes(int kmax, int ld, int jb, int n2)
+{
+    const long walk = 16L * kLS * (2L * ld + 2L * n2);
+    const long contraction = ((8L * kLS * kmax + 15) & ~15L) + 16L * jb * ld;
+    return walk > contraction ? walk : contraction;
+}
+
 __host__ __device__ inline int bwd_warp_smem_bytes(int kmax, int ld, int jb, int n2)
 {
-    long bytes = 16L * (kmax * ld + ld + 3L * kLS * ld + 2L * kLS * n2 + kLS * (long)jb * ld) + 8L * 32 +
-                 8L * kLS * (long)kmax + 4L * (16 + ld + kmax);
+    long bytes = 16L * (kmax * ld + ld + kLS * (long)ld + kLS * (long)jb * ld) +
+                 bwd_walk_region_bytes(kmax, ld, jb, n2) + 8L * 32 + 4L * (16 + ld + kmax);
     return (int)((bytes + 15) & ~15L);
 }
 
 struct BwdSmem {
     double2* M;       // kmax x ld
     double2* base;    // ld
-    double2* S;       // ld x kLS (lane-major: element (j, lane) at j * kLS + lane)
-    double2* A;       // ld x kLS
+    double2* A;       // ld x kLS (lane-major: element (j, lane) at j * kLS + lane)
+    double2* C;       // jb x ld x kLS
+    double2* S;       // ld x kLS        -- walk region
     double2* P;       // ld x kLS
     double2* PW;      // n2 x kLS
     double2* FULL;    // n2 x kLS
-    double2* C;       // jb x ld x kLS
+    double* X;        // kmax x kLS      -- the same region at the end of a task
+    double2* V;       // jb x ld
     double* wh;       // 32
-    double* x;        // kmax x kLS: row multipliers x_i of each lane, then wh x_i
     int32_t* lowrow;  // 16
     int32_t* cm;      // ld
     int32_t* rowdig;  // kmax: low digit of each row, or -1
@@ -67,15 +80,18 @@ struct BwdSmem {
         ld = ld_;
         M = reinterpret_cast<double2*>(raw);
         base = M + kmax * ld;
-        S = base + ld;
-        A = S + kLS * ld;
-        P = A + kLS * ld;
+        A = base + ld;
+        C = A + kLS * ld;
+        S = C + kLS * jb * ld;
+        P = S + kLS * ld;
         PW = P + kLS * ld;
         FULL = PW + kLS * n2;
-        C = FULL + kLS * n2;
-        wh = reinterpret_cast<double*>(C + kLS * jb * ld);
-        x = wh + 32;
-        lowrow = reinterpret_cast<int32_t*>(x + kmax * kLS);
+        X = reinterpret_cast<double*>(S);
+        V = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(S) +
+                                       ((8L * kLS * kmax + 15) & ~15L));
+        wh = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(S) +
+                                       bwd_walk_region_bytes(kmax, ld, jb, n2));
+        lowrow = reinterpret_cast<int32_t*>(wh + 32);
         cm = lowrow + 16;
         rowdig = cm + ld;
     }
@@ -96,6 +112,12 @@ __device__ __forceinline__ void acc_scaled(double2* a, double s, double2 q)
 // are stored; the suffix sw = ws prod_{j' > j} S_{j'}^{c_{j'}} carries the
 // term's weight, so that every column's accumulation A_j += P_j sw (times PW_j
 // for a repeated column) is one fused complex multiply-add.
+//
+// Every loop over columns loads the next column's operands from shared
+// memory before it computes the current one (the index of the last column
+// is reused instead of reading past it): with only a few warps per SM
+// sub-partition a load waited for inside the loop would leave the FP64 pipe
+// idle.
 __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* PW, double2* FULL,
                                          double2* A, int l, int n2, const int32_t* cm, double ws)
 {
@@ -112,30 +134,52 @@ __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* 
         return;
     }
     // powers of the repeated columns
+    if (n2 > 0) {
+        double2 sn = S[0];
+        int cn = cm[0];
 #pragma unroll 1
-    for (int j = 0; j < n2; ++j) {
-        const double2 s = S[j * kLS];
-        double2 pw = s;
+        for (int j = 0; j < n2; ++j) {
+            const double2 s = sn;
+            const int c = cn;
+            const int jn = j + 1 < n2 ? j + 1 : j;
+            sn = S[jn * kLS];
+            cn = cm[jn];
+            double2 pw = s;
 #pragma unroll 1
-        for (int e = 2; e < cm[j]; ++e)
-            pw = cmul(pw, s);
-        FULL[j * kLS] = cmul(pw, s);
-        const double c = (double)cm[j];
-        PW[j * kLS] = make_double2(__dmul_rn(c, pw.x), __dmul_rn(c, pw.y));
+            for (int e = 2; e < c; ++e)
+                pw = cmul(pw, s);
+            FULL[j * kLS] = cmul(pw, s);
+            const double cd = (double)c;
+            PW[j * kLS] = make_double2(__dmul_rn(cd, pw.x), __dmul_rn(cd, pw.y));
+        }
     }
-    // prefix P_j = prod_{j' < j} S_{j'}^{c_{j'}}, j = 1 .. l-1
+    // prefix P_j = prod_{j' < j} S_{j'}^{c_{j'}}, j = 1 .. l-1: FULL for the
+    // repeated columns among 1 .. l-2, then S
     double2 run = (n2 > 0) ? FULL[0] : S[0];
     P[kLS] = run;
-    const int na = n2 < l - 1 ? n2 : l - 1;  // repeated columns among 1 .. l-2
+    const int na = n2 < l - 1 ? n2 : l - 1;
+    if (na > 1) {
+        double2 fn = FULL[kLS];
 #pragma unroll 1
-    for (int j = 1; j < na; ++j) {
-        run = cmul(run, FULL[j * kLS]);
-        P[(j + 1) * kLS] = run;
+        for (int j = 1; j < na; ++j) {
+            const double2 f = fn;
+            fn = FULL[(j + 1 < na ? j + 1 : j) * kLS];
+            run = cmul(run, f);
+            P[(j + 1) * kLS] = run;
+        }
     }
+    {
+        const int j0 = na > 1 ? na : 1;
+        if (j0 < l - 1) {
+            double2 sn = S[j0 * kLS];
 #pragma unroll 1
-    for (int j = (na > 1 ? na : 1); j < l - 1; ++j) {
-        run = cmul(run, S[j * kLS]);
-        P[(j + 1) * kLS] = run;
+            for (int j = j0; j < l - 1; ++j) {
+                const double2 sv = sn;
+                sn = S[(j + 1 < l - 1 ? j + 1 : j) * kLS];
+                run = cmul(run, sv);
+                P[(j + 1) * kLS] = run;
+            }
+        }
     }
     // suffix pass, last column first
     double2 sw;
@@ -152,22 +196,46 @@ __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* 
         acc_scaled(A + j * kLS, ws, q);
         sw = make_double2(__dmul_rn(ws, f.x), __dmul_rn(ws, f.y));
     }
-    // columns l-2 .. 1 with c_j = 1
+    // columns l-2 .. max(n2, 1) with c_j = 1
+    {
+        const int jlo = n2 > 1 ? n2 : 1;
+        int j = l - 2;
+        if (j >= jlo) {
+            double2 pn = P[j * kLS], an = A[j * kLS], sn = S[j * kLS];
 #pragma unroll 1
-    for (int j = l - 2; j >= 1 && j >= n2; --j) {
-        double2 av = A[j * kLS];
-        cfma_acc<false>(av, P[j * kLS], sw);
-        A[j * kLS] = av;
-        sw = cmul(sw, S[j * kLS]);
+            for (; j >= jlo; --j) {
+                const double2 pv = pn, sv = sn;
+                double2 av = an;
+                const int jn = j - 1 >= jlo ? j - 1 : j;
+                pn = P[jn * kLS];
+                an = A[jn * kLS];
+                sn = S[jn * kLS];
+                cfma_acc<false>(av, pv, sw);
+                A[j * kLS] = av;
+                sw = cmul(sw, sv);
+            }
+        }
     }
     // columns min(n2, l-1) - 1 .. 1 with c_j >= 2
+    {
+        int j = (n2 < l - 1 ? n2 : l - 1) - 1;
+        if (j >= 1) {
+            double2 pn = P[j * kLS], an = A[j * kLS], wn = PW[j * kLS], fn = FULL[j * kLS];
 #pragma unroll 1
-    for (int j = (n2 < l - 1 ? n2 : l - 1) - 1; j >= 1; --j) {
-        const double2 q = cmul(P[j * kLS], sw);
-        double2 av = A[j * kLS];
-        cfma_acc<false>(av, q, PW[j * kLS]);
-        A[j * kLS] = av;
-        sw = cmul(sw, FULL[j * kLS]);
+            for (; j >= 1; --j) {
+                const double2 pv = pn, wv = wn, fv = fn;
+                double2 av = an;
+                const int jn = j - 1 >= 1 ? j - 1 : j;
+                pn = P[jn * kLS];
+                an = A[jn * kLS];
+                wn = PW[jn * kLS];
+                fn = FULL[jn * kLS];
+                const double2 q = cmul(pv, sw);
+                cfma_acc<false>(av, q, wv);
+                A[j * kLS] = av;
+                sw = cmul(sw, fv);
+            }
+        }
     }
     // column 0: Q_0 = c_0 S_0^{c_0 - 1} * prod_{j > 0}
     double2 av = A[0];
@@ -230,7 +298,7 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
         }
         const int64_t chunk0 = (int64_t)t.part * kWarp;
         const bool active = chunk0 + lane < D.nchunks;
-        int64_t c = active ? (chunk0 + lane) : 0;
+        const int64_t chunk = active ? (chunk0 + lane) : 0;
         double2* S = sm.S + lane;
         double2* A = sm.A + lane;
 #pragma unroll 1
@@ -238,31 +306,33 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
             S[j * kLS] = sm.base[j];
             A[j * kLS] = make_double2(0.0, 0.0);
         }
-        for (int i = 0; i < k; ++i)
-            sm.x[i * kLS + lane] = (double)mv.rmul[i];
+        // the high digits of this lane's chunk: column sums and weight
         uint64_t whigh_u = 1;
         int gpar = 0;
+        int64_t c = chunk;
 #pragma unroll 1
         for (int d = J; d < ndig; ++d) {
             const int rad = mv.drad[d];
             const int g = (int)(c % rad);
             c /= rad;
-            const int row = mv.drow[d];
-            const double2* Mr = sm.M + row * sm.ld;
+            if (g == 0)
+                continue;
+            const double2* Mr = sm.M + mv.drow[d] * sm.ld;
             const double coef = (double)(-2 * g);
+            double2 bn = Mr[0], sn = S[0];
 #pragma unroll 1
             for (int j = 0; j < l; ++j) {
-                const double2 b = Mr[j];
-                double2 s = S[j * kLS];
-                s.x = __fma_rn(coef, b.x, s.x);
-                s.y = __fma_rn(coef, b.y, s.y);
-                S[j * kLS] = s;
+                const double2 b = bn;
+                double2 sv = sn;
+                const int jn = j + 1 < l ? j + 1 : j;
+                bn = Mr[jn];
+                sn = S[jn * kLS];
+                sv.x = __fma_rn(coef, b.x, sv.x);
+                sv.y = __fma_rn(coef, b.y, sv.y);
+                S[j * kLS] = sv;
             }
-            sm.x[row * kLS + lane] = (double)(mv.rmul[row] - 2 * g);
-            if (g) {
-                whigh_u *= binom_u64(mv.dtop[d], g);
-                gpar += g;
-            }
+            whigh_u *= binom_u64(mv.dtop[d], g);
+            gpar += g;
         }
         double whigh = active ? (double)whigh_u : 0.0;
         if (gpar & 1)
@@ -299,15 +369,19 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
                 const double delta = up > 0 ? -2.0 : 2.0;
                 const double2* Mr = sm.M + row * sm.ld;
                 double2* Cd = sm.C + d * sm.ld * kLS + lane;
+                double2 bn = Mr[0], svn = S[0], avn = A[0], cvn = Cd[0];
 #pragma unroll 1
                 for (int j = 0; j < l; ++j) {
-                    const double2 b = Mr[j];
-                    double2 sv = S[j * kLS];
+                    const double2 b = bn, av = avn;
+                    double2 sv = svn, cv = cvn;
+                    const int jn = j + 1 < l ? j + 1 : j;
+                    bn = Mr[jn];
+                    svn = S[jn * kLS];
+                    avn = A[jn * kLS];
+                    cvn = Cd[jn * kLS];
                     sv.x = __fma_rn(delta, b.x, sv.x);
                     sv.y = __fma_rn(delta, b.y, sv.y);
                     S[j * kLS] = sv;
-                    const double2 av = A[j * kLS];
-                    double2 cv = Cd[j * kLS];
                     cv.x = __fma_rn(delta, av.x, cv.x);
                     cv.y = __fma_rn(delta, av.y, cv.y);
                     Cd[j * kLS] = cv;
@@ -316,23 +390,33 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
                     wlow = (double)low_weight(wk, J);
             }
         }
-        __syncwarp();
         // Contraction G_ij = sum_q wh_q (x_iq A_jq - C_{d(i) j q}) over the 32
         // lanes q in order, as sum_q u_iq A_jq - V_{d(i) j} with u_iq = wh_q x_iq
         // and V_dj = sum_q wh_q C_djq, so that each product is formed once.
-        // Low-digit rows end the chunk at the walk's final Gray value, which
-        // every lane shares.
-        for (int d = 0; d < J; ++d) {
-            const int g = (int)((wk.g >> (4 * d)) & 15u);
-            const int row = sm.lowrow[d];
-            sm.x[row * kLS + lane] = (double)(mv.rmul[row] - 2 * g);
-        }
+        // The walk region (S, P, PW, FULL) is free now and holds u and V.
+        // x_i = r_i - 2 g_i: rows without a digit keep r_i, high-digit rows
+        // take g from this lane's chunk index, low-digit rows from the walk's
+        // final Gray value, which every lane shares.
+        __syncwarp();
         {
             const double whl = sm.wh[lane];
+            double* X = sm.X + lane;
             for (int i = 0; i < k; ++i)
-                sm.x[i * kLS + lane] *= whl;
+                X[i * kLS] = whl * (double)mv.rmul[i];
+            int64_t cc = chunk;
+            for (int d = J; d < ndig; ++d) {
+                const int rad = mv.drad[d];
+                const int g = (int)(cc % rad);
+                cc /= rad;
+                const int row = mv.drow[d];
+                X[row * kLS] = whl * (double)(mv.rmul[row] - 2 * g);
+            }
+            for (int d = 0; d < J; ++d) {
+                const int g = (int)((wk.g >> (4 * d)) & 15u);
+                const int row = sm.lowrow[d];
+                X[row * kLS] = whl * (double)(mv.rmul[row] - 2 * g);
+            }
         }
-        double2* V = sm.P;  // the prefixes are no longer needed: J x ld entries
         __syncwarp();
         for (int e = lane; e < J * l; e += kWarp) {
             const int d = e / l, j = e - d * l;
@@ -343,14 +427,14 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
                 vx = __fma_rn(sm.wh[q], cv.x, vx);
                 vy = __fma_rn(sm.wh[q], cv.y, vy);
             }
-            V[d * sm.ld + j] = make_double2(vx, vy);
+            sm.V[d * sm.ld + j] = make_double2(vx, vy);
         }
         __syncwarp();
         for (int e = lane; e < kl; e += kWarp) {
             const int i = e / l, j = e - i * l;
             const int dg = sm.rowdig[i];
             const double2* Aq = sm.A + j * kLS;
-            const double* uq = sm.x + i * kLS;
+            const double* uq = sm.X + i * kLS;
             double gx = 0.0, gy = 0.0;
             for (int q = 0; q < 32; ++q) {
                 const double2 av = Aq[q];
@@ -358,7 +442,7 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
                 gy = __fma_rn(uq[q], av.y, gy);
             }
             if (dg >= 0) {
-                const double2 v = V[dg * sm.ld + j];
+                const double2 v = sm.V[dg * sm.ld + j];
                 gx = __dsub_rn(gx, v.x);
                 gy = __dsub_rn(gy, v.y);
             }
@@ -427,10 +511,11 @@ __device__ __forceinline__ int32_t bwd_guard(const BwdArgs& a, int64_t ti, int k
 
 // Tasks [t_begin, t_end) of the list; a task whose guards fail is skipped
 // and recorded in the error record.
-// At least 3 blocks of 256 threads per SM caps the kernel at 85 registers per
-// thread; it needs 80 without spilling, and without the cap the guards' extra
-// branch in the task loop lets the allocator take 104.
-__global__ void __launch_bounds__(256, 3) glynn_bwd_kernel(BwdArgs a, int64_t t_begin,
+// At least 2 blocks of 256 threads per SM caps the kernel at 128 registers
+// per thread (it takes 118 without spilling, the prefetched operands of the
+// column loops included): 17 warps per SM, more than the shared-memory
+// workspace of every class but the narrowest leaves room for.
+__global__ void __launch_bounds__(256, 2) glynn_bwd_kernel(BwdArgs a, int64_t t_begin,
                                                          int64_t t_end, int kmax, int ld, int jb,
                                                          int n2, int queue)
 {

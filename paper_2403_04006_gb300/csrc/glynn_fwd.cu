@@ -223,6 +223,8 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
             const int rad = mv.drad[d];
             const int g = (int)(c % rad);
             c /= rad;
+            if (g == 0)  // no sign flip in this row: nothing to do (for the whole warp, often)
+                continue;
             const double2* Mr = sm.M + mv.drow[d] * sm.ld;
             const double coef = (double)(-2 * g);
 #pragma unroll 1
@@ -233,10 +235,8 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
                 s.y = __fma_rn(coef, b.y, s.y);
                 S[j * 32] = s;
             }
-            if (g) {
-                whigh_u *= binom_u64(mv.dtop[d], g);
-                gpar += g;
-            }
+            whigh_u *= binom_u64(mv.dtop[d], g);
+            gpar += g;
         }
         double whigh = active ? (double)whigh_u : 0.0;
         if (gpar & 1)
