@@ -31,7 +31,9 @@ forward on a 4096-permanent batch of the recipe or the n = 30 permanent;
 per product-column class and the scatter) on the benchmark batch or the
 4096-permanent batch; ``hafnian-2x`` and
 ``loop-hafnian-2x`` time the repeated (loop) hafnian of a k x k GBS matrix
-with every index repeated twice (``--k``); ``fp64-sweep`` measures the FP64
+with every index repeated twice (``--k``); ``gradient-m16`` times the
+Clements mesh (m = 16) -> 1024 boson-sampling probabilities -> sum ->
+backward through both; ``fp64-sweep`` measures the FP64
 pipe (DFMA, DADD, DMUL) against resident warps per SM and independent chains
 per thread.
 """
@@ -191,7 +193,7 @@ def profiled_traffic():
 
 
 PROFILE_CASES = ("ragged-backward", "ragged4096-backward", "hafnian-2x", "loop-hafnian-2x",
-                 "fp64-sweep")
+                 "gradient-m16", "fp64-sweep")
 
 
 def load_workload(name: str, block: int = 0):
@@ -639,6 +641,19 @@ def bench_case(args, dev):
         terms_of = lambda: plan.stats()["terms"]  # noqa: E731
         if args.workload == "ragged4096-backward":
             desc = desc.replace("(profiling case)", "backward (profiling case)")
+    elif args.workload == "gradient-m16":
+        th, ph, s5, t5 = W.gradient_workload()
+        thd = torch.from_numpy(th).to(dev).requires_grad_(True)
+        phd = torch.from_numpy(ph).to(dev).requires_grad_(True)
+        sd5, td5 = torch.from_numpy(s5).to(dev), torch.from_numpy(t5).to(dev)
+        plan5 = api.Plan.for_bs(16, s5, t5)
+
+        def op():
+            U5 = api.ClementsMesh.apply(thd, phd, 16)
+            api.BSProbs.apply(U5, sd5, td5, plan5).sum().backward()
+        terms_of = lambda: plan5.stats()["terms"]  # noqa: E731
+        desc = ("Clements mesh m = 16 (120 beamsplitters) -> probabilities of 1024 patterns with "
+                "8 photons -> sum -> backward (profiling case)")
     else:
         loop = args.workload.startswith("loop")
         B, r, g = W.paper_repeated_hafnian(args.k, loop=loop)
