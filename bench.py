@@ -243,13 +243,24 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+ARM_PARTS = {"0xd0c": "Neoverse N1", "0xd40": "Neoverse V1", "0xd49": "Neoverse N2",
+             "0xd4f": "Neoverse V2", "0xd8e": "Neoverse N3", "0xd84": "Neoverse V3"}
+
+
 def cpu_model() -> str:
+    """The host CPU's model name, or for Arm cores the name of their part number."""
+    part = None
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part", "hardware")):
+            key = line.split(":", 1)[0].strip().lower()
+            if key == "model name":
                 return line.split(":", 1)[1].strip()
+            if key == "cpu part" and part is None:
+                part = line.split(":", 1)[1].strip().lower()
     except OSError:
         pass
+    if part is not None:
+        return f"Arm {ARM_PARTS.get(part, 'part ' + part)}"
     return "unknown"
 
 

@@ -7,7 +7,9 @@
 //
 // Forward: U starts as the identity in shared memory; each layer updates the
 // two rows of every pair (pairs of one layer are disjoint, so a layer is one
-// parallel step).
+// parallel step).  Both kernels first take sin and cos of every angle once
+// into shared memory: a beamsplitter's block is used for every row or column
+// it touches, and FP64 sincos is dear on this GPU.
 //
 // Adjoint: with G = dL/dRe U + i dL/dIm U and W = G U^H,
 //   dL/dtheta_k = Re sum_{a,b in pair} conj((W_k T_k)_ab) (dT_k/dtheta)_ab,
@@ -34,11 +36,24 @@ struct Blk {
     double2 a00, a01, a10, a11;
 };
 
-__device__ __forceinline__ Blk bs_block(double th, double ph)
+// cos theta_k, sin theta_k, cos phi_k, sin phi_k of every beamsplitter, at
+// trig[4k .. 4k+3].
+__device__ void load_trig(const double* theta, const double* phi, int L, double* trig)
 {
-    double s, c, sp, cp;
-    sincos(th, &s, &c);
-    sincos(ph, &sp, &cp);
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        double s, c, sp, cp;
+        sincos(theta[k], &s, &c);
+        sincos(phi[k], &sp, &cp);
+        trig[4 * k + 0] = c;
+        trig[4 * k + 1] = s;
+        trig[4 * k + 2] = cp;
+        trig[4 * k + 3] = sp;
+    }
+}
+
+__device__ __forceinline__ Blk bs_block(const double* trig, int k)
+{
+    const double c = trig[4 * k], s = trig[4 * k + 1], cp = trig[4 * k + 2], sp = trig[4 * k + 3];
     Blk b;
     b.a00 = make_double2(c, 0.0);
     b.a01 = make_double2(-cp * s, sp * s);  // -conj(e^{i phi} sin)
@@ -50,7 +65,9 @@ __device__ __forceinline__ Blk bs_block(double th, double ph)
 __global__ void __launch_bounds__(256) clements_fwd_kernel(const double* theta, const double* phi,
                                                            int m, double2* U)
 {
-    extern __shared__ double2 sh[];  // m x m
+    extern __shared__ double2 sh[];  // m x m, then the angles' sin and cos
+    double* trig = reinterpret_cast<double*>(sh + m * m);
+    load_trig(theta, phi, m * (m - 1) / 2, trig);
     for (int e = threadIdx.x; e < m * m; e += blockDim.x)
         sh[e] = make_double2((e / m == e % m) ? 1.0 : 0.0, 0.0);
     __syncthreads();
@@ -60,7 +77,7 @@ __global__ void __launch_bounds__(256) clements_fwd_kernel(const double* theta, 
         for (int w = threadIdx.x; w < np * m; w += blockDim.x) {
             const int pi = w / m, col = w - pi * m;
             const int j = (q & 1) + 2 * pi;
-            const Blk b = bs_block(theta[kbase + pi], phi[kbase + pi]);
+            const Blk b = bs_block(trig, kbase + pi);
             const double2 u0 = sh[j * m + col], u1 = sh[(j + 1) * m + col];
             sh[j * m + col] = c_add(c_mul(b.a00, u0), c_mul(b.a01, u1));
             sh[(j + 1) * m + col] = c_add(c_mul(b.a10, u0), c_mul(b.a11, u1));
@@ -77,7 +94,9 @@ __global__ void __launch_bounds__(256) clements_adj_kernel(const double* theta, 
                                                            const double2* G, double* gtheta,
                                                            double* gphi)
 {
-    extern __shared__ double2 W[];  // m x m
+    extern __shared__ double2 W[];  // m x m, then the angles' sin and cos
+    double* trig = reinterpret_cast<double*>(W + m * m);
+    load_trig(theta, phi, m * (m - 1) / 2, trig);
     // W = G U^H
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int a = e / m, b = e - a * m;
@@ -94,8 +113,7 @@ __global__ void __launch_bounds__(256) clements_adj_kernel(const double* theta, 
         // gradients of this layer from the 2 x 2 blocks of W T
         for (int pi = threadIdx.x; pi < np; pi += blockDim.x) {
             const int j = (q & 1) + 2 * pi;
-            const double th = theta[kbase + pi], ph = phi[kbase + pi];
-            const Blk b = bs_block(th, ph);
+            const Blk b = bs_block(trig, kbase + pi);
             const double2 w00 = W[j * m + j], w01 = W[j * m + j + 1];
             const double2 w10 = W[(j + 1) * m + j], w11 = W[(j + 1) * m + j + 1];
             // M = Wblk * Blk
@@ -103,9 +121,8 @@ __global__ void __launch_bounds__(256) clements_adj_kernel(const double* theta, 
             const double2 m01 = c_add(c_mul(w00, b.a01), c_mul(w01, b.a11));
             const double2 m10 = c_add(c_mul(w10, b.a00), c_mul(w11, b.a10));
             const double2 m11 = c_add(c_mul(w10, b.a01), c_mul(w11, b.a11));
-            double s, c, sp, cp;
-            sincos(th, &s, &c);
-            sincos(ph, &sp, &cp);
+            const double c = trig[4 * (kbase + pi)], s = trig[4 * (kbase + pi) + 1];
+            const double cp = trig[4 * (kbase + pi) + 2], sp = trig[4 * (kbase + pi) + 3];
             // dT/dtheta = [[-s, -e^{-i phi} c], [e^{i phi} c, -s]]
             const double2 t00 = make_double2(-s, 0.0), t01 = make_double2(-cp * c, sp * c);
             const double2 t10 = make_double2(cp * c, sp * c), t11 = make_double2(-s, 0.0);
@@ -122,7 +139,7 @@ __global__ void __launch_bounds__(256) clements_adj_kernel(const double* theta, 
         for (int w = threadIdx.x; w < np * m; w += blockDim.x) {
             const int pi = w / m, row = w - pi * m;
             const int j = (q & 1) + 2 * pi;
-            const Blk b = bs_block(theta[kbase + pi], phi[kbase + pi]);
+            const Blk b = bs_block(trig, kbase + pi);
             const double2 x0 = W[row * m + j], x1 = W[row * m + j + 1];
             W[row * m + j] = c_add(c_mul(x0, b.a00), c_mul(x1, b.a10));
             W[row * m + j + 1] = c_add(c_mul(x0, b.a01), c_mul(x1, b.a11));
@@ -132,7 +149,7 @@ __global__ void __launch_bounds__(256) clements_adj_kernel(const double* theta, 
         for (int w = threadIdx.x; w < np * m; w += blockDim.x) {
             const int pi = w / m, col = w - pi * m;
             const int j = (q & 1) + 2 * pi;
-            const Blk b = bs_block(theta[kbase + pi], phi[kbase + pi]);
+            const Blk b = bs_block(trig, kbase + pi);
             const double2 y0 = W[j * m + col], y1 = W[(j + 1) * m + col];
             // (T^H)_{00} = conj(a00), (T^H)_{01} = conj(a10), (T^H)_{10} = conj(a01), (T^H)_{11} = conj(a11)
             W[j * m + col] = c_add(c_mul(c_conj(b.a00), y0), c_mul(c_conj(b.a10), y1));
@@ -149,7 +166,7 @@ static cudaError_t ensure_attrs()
 {
     if (g_attr_set)
         return cudaSuccess;
-    const int bytes = 64 * 64 * 16;
+    const int bytes = 64 * 64 * 16 + 32 * (64 * 63 / 2);  // m <= 64: U or W, and the angles
     cudaError_t e = cudaFuncSetAttribute(clements_fwd_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
@@ -166,7 +183,7 @@ cudaError_t clements_forward(const double* theta, const double* phi, int m, doub
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess)
         return e;
-    clements_fwd_kernel<<<1, 256, m * m * 16, st>>>(theta, phi, m, U);
+    clements_fwd_kernel<<<1, 256, m * m * 16 + 32 * (m * (m - 1) / 2), st>>>(theta, phi, m, U);
     return cudaGetLastError();
 }
 
@@ -176,7 +193,8 @@ cudaError_t clements_backward(const double* theta, const double* phi, int m, con
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess)
         return e;
-    clements_adj_kernel<<<1, 256, m * m * 16, st>>>(theta, phi, m, U, gU, gtheta, gphi);
+    clements_adj_kernel<<<1, 256, m * m * 16 + 32 * (m * (m - 1) / 2), st>>>(theta, phi, m, U, gU,
+                                                                          gtheta, gphi);
     return cudaGetLastError();
 }
 

@@ -180,3 +180,34 @@ def test_shards_balance_small_permanents(dev):
         held.append(int((np.abs(p).sum(axis=1) > 0).sum()))
     assert sum(held) == pb.batch
     assert min(held) >= pb.batch // R - 1
+
+
+def test_tune_cache_under_the_current_device_name(dev, tmp_path):
+    """Without a key the cache is filed under this GPU's name and SM count;
+    a plan made after loading it uses the stored chunk lengths (2^5 terms for
+    n = 16, against the default 2^10: many more warp tasks) and still gives
+    the oracle's permanent."""
+    import json
+    A = W.single_large(16)
+    pb = W.pack_batch([(A, [1] * 16, [1] * 16)])
+    saved = pq.pq_tune_table_get()
+    try:
+        pq.pq_tune_table_set(np.zeros(pq.PQ_MAX_N + 1, dtype=np.int32))
+        default_tasks = api.Plan.for_batch(pb).stats()["tasks"]
+        t = np.zeros(pq.PQ_MAX_N + 1, dtype=np.int32)
+        t[16] = 5
+        pq.pq_tune_table_set(t)
+        path = str(tmp_path / "tune.json")
+        pq.pq_tune_cache_save(path)
+        key, = json.load(open(path))["tables"].keys()
+        assert torch.cuda.get_device_name(0) in key and "SMs" in key
+        pq.pq_tune_table_set(np.zeros_like(t))
+        assert pq.pq_tune_cache_load(path)
+        assert pq.pq_tune_table_get()[16] == 5
+        plan = api.Plan.for_batch(pb)
+        assert plan.stats()["tasks"] >= 8 * default_tasks
+        got = api.permanent_batched(api.DeviceBatch(pb, dev), plan).cpu().numpy()[0]
+        ref = O.perm_ryser(A, gold=True)
+        assert abs(got - ref) <= 1e-10 * abs(ref)
+    finally:
+        pq.pq_tune_table_set(saved)
