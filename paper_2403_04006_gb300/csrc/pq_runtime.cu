@@ -45,10 +45,12 @@ cudaError_t dev_alloc(void** p, size_t bytes)
     if (hook_fails())
         return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(p, bytes);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
         g_live_device.fetch_add(1);
-    else
+    } else {
         *p = nullptr;
+        cudaGetLastError();  // the failure is reported here, not by a later launch check
+    }
     return e;
 }
 
@@ -200,6 +202,8 @@ struct JsonReader {
             double v;
             if (!number(v))
                 return false;
+            if (!(v >= -2147483648.0 && v <= 2147483647.0))  // also rejects NaN
+                return ok = false;
             out.push_back((int32_t)v);
         } while (eat(','));
         return eat(']') || (ok = false);
