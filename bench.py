@@ -322,8 +322,9 @@ def bench_ours(args):
         return bench_case(args, dev)
     pb, workload_desc = load_workload(args.workload, block=rank)
     db = api.DeviceBatch(pb, dev)
-    plan = api.Plan.for_batch(pb, method="batched", use_graph=True)
-    plan.autotune(db)
+    plan = api.Plan.for_batch(pb, method="batched", use_graph=True, chunk_log2=args.chunk_log2)
+    if not args.no_autotune and args.chunk_log2 == 0:
+        plan.autotune(db)
     st = plan.stats()
     out = torch.empty(pb.batch, dtype=torch.complex128, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -429,7 +430,9 @@ def bench_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": bench_config(WORKLOAD if args.workload == "ragged" else workload_desc,
                                int(job_perms), int(job_terms), world),
-        "method": "batched persistent kernel, CUDA graph, autotuned chunks",
+        "method": "batched persistent kernel, CUDA graph, " + (
+            f"chunks of about 2^{args.chunk_log2} terms" if args.chunk_log2 else
+            "default chunks" if args.no_autotune else "autotuned chunks"),
         "permanents_per_s": perms_per_s,
         "roofline": {"bound": "alu", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s",
@@ -758,6 +761,10 @@ def main(argv=None):
     ap.add_argument("--quick", action="store_true", help="skip the extra measurements")
     ap.add_argument("--workload", choices=["ragged", "ragged4096", "single30", *PROFILE_CASES],
                     default="ragged", help="ragged is the benchmark; the others are profiling cases")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plan with the built-in chunk lengths instead of timing candidates first")
+    ap.add_argument("--chunk-log2", type=int, default=0,
+                    help="plan every permanent with chunks of about 2^K terms (0: per class)")
     ap.add_argument("--k", type=int, default=18,
                     help="hafnian profiling cases: base size k (N = 2k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
