@@ -588,22 +588,23 @@ __global__ void scatter_batch_kernel(const PermDesc* desc, const int32_t* meta,
 // (for a pattern whose summed side is its input modes the roles swap in the
 // planner, which writes the map accordingly).
 //
-// One warp per entry (a, c): lane q adds the patterns [q B / 32, (q + 1) B / 32)
-// in order, then a fixed shuffle tree adds the 32 lane sums, so the result
-// is the same on every run and no floating-point atomics are needed.  The
-// loads of one pattern (map, descriptor, gradient block) are independent of
-// the next pattern's, so a lane keeps several in flight.
-__global__ void __launch_bounds__(256) scatter_bs_kernel(const PermDesc* desc, int64_t nperm,
-                                                         int m, const int32_t* pos,
-                                                         const double2* gl, const int64_t* gl_off,
-                                                         double2* gU)
+// One block of kScatterThreads threads per entry (a, c): thread q adds the
+// patterns [q B / T, (q + 1) B / T) in order, each warp adds its 32 sums with
+// a fixed shuffle tree and the first thread adds the warp sums in warp order,
+// so the result is the same on every run and no floating-point atomics are
+// needed.  The loads of one pattern (map, descriptor, gradient block) are
+// independent of the next pattern's, so a thread keeps several in flight.
+constexpr int kScatterThreads = 128;
+
+__global__ void __launch_bounds__(kScatterThreads) scatter_bs_kernel(
+    const PermDesc* desc, int64_t nperm, int m, const int32_t* pos, const double2* gl,
+    const int64_t* gl_off, double2* gU)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (e >= (int64_t)m * m)
-        return;  // e is the same for the whole warp
+    __shared__ double2 wsum[kScatterThreads / kWarp];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t e = blockIdx.x;  // < m * m by the launch
     const int ar = (int)(e / m), ac = (int)(e - (int64_t)ar * m);  // U row (output), column (input)
-    const int64_t p0 = nperm * lane / kWarp, p1 = nperm * (lane + 1) / kWarp;
+    const int64_t p0 = nperm * tid / kScatterThreads, p1 = nperm * (tid + 1) / kScatterThreads;
     double gx = 0.0, gy = 0.0;
 #pragma unroll 4
     for (int64_t p = p0; p < p1; ++p) {
@@ -623,7 +624,16 @@ __global__ void __launch_bounds__(256) scatter_bs_kernel(const PermDesc* desc, i
         gy += __shfl_down_sync(0xffffffffu, gy, off);
     }
     if (lane == 0)
-        gU[e] = make_double2(gx, gy);
+        wsum[warp] = make_double2(gx, gy);
+    __syncthreads();
+    if (tid == 0) {
+        double2 t = wsum[0];
+        for (int w = 1; w < kScatterThreads / kWarp; ++w) {
+            t.x += wsum[w].x;
+            t.y += wsum[w].y;
+        }
+        gU[e] = t;
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -686,10 +696,11 @@ cudaError_t scatter_grad_bs(const PermDesc* desc, const int32_t* pos, int64_t np
                             const double2* grad_local, const int64_t* grad_local_off,
                             double2* grad_U, cudaStream_t st)
 {
-    const int warps_per_block = 8;  // one warp per entry of grad_U
-    const int blocks = (m * m + warps_per_block - 1) / warps_per_block;
-    scatter_bs_kernel<<<blocks, 32 * warps_per_block, 0, st>>>(desc, nperm, m, pos, grad_local,
-                                                               grad_local_off, grad_U);
+    if (m <= 0)
+        return cudaSuccess;
+    scatter_bs_kernel<<<(unsigned)(m * m), kScatterThreads, 0, st>>>(desc, nperm, m, pos,
+                                                                     grad_local, grad_local_off,
+                                                                     grad_U);
     return cudaGetLastError();
 }
 

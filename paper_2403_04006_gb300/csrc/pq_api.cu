@@ -1467,8 +1467,13 @@ extern "C" int pq_clements_backward(const double* theta, const double* phi, int3
 }
 
 // ---------------------------------------------------------------- autotuning
-// For every photon number present, try chunk lengths 2^4 .. 2^12 (one class at
-// a time, the others fixed) on the plan's own data and keep the fastest.
+// For every photon number present (a size class), time the class's own
+// permanents -- a temporary plan of just those items, reading the same matrix
+// data -- with the current chunk cap (the incumbent) and with caps of 2^4 ..
+// 2^14 terms, and keep a candidate only if it is at least 1% faster than the
+// incumbent.  Timing each class on its own matters: a small class changes
+// the whole batch's time by less than the timing noise, and a choice made
+// from whole-batch times can then only be noise.
 extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void* stream)
 {
     if (!P)
@@ -1496,22 +1501,17 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    std::vector<int> present(PQ_MAX_N + 1, 0);
+    std::vector<std::vector<ItemPlan>> by_n(PQ_MAX_N + 1);
     for (const ItemPlan& it : P->items)
         if (!it.trivial)
-            present[it.n] = 1;
-    const int saved_opt = P->opts.chunk_log2;
-    P->opts.chunk_log2 = 0;
-    const int cands[] = {4, 6, 8, 10, 12};
+            by_n[it.n].push_back(it);
     int rc = PQ_OK;
-    auto time_once = [&](float& ms) -> int {
-        int r = schedule_and_upload(P);
-        if (r != PQ_OK)
-            return r;
+    // time one execution of plan T (best of 5 after a warm-up)
+    auto time_plan = [&](pq_plan* T, float& ms) -> int {
         float best = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 6; ++rep) {
             cudaEventRecord(e0, st);
-            r = run_forward_raw(P, src, amps, nullptr, st);
+            int r = run_forward_raw(T, src, amps, nullptr, st);
             if (r != PQ_OK)
                 return r;
             cudaEventRecord(e1, st);
@@ -1520,31 +1520,60 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
                 return fail(PQ_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
             float t = 0.0f;
             cudaEventElapsedTime(&t, e0, e1);
-            best = std::min(best, t);
+            if (rep > 0)
+                best = std::min(best, t);
         }
         ms = best;
         return PQ_OK;
     };
+    const int cands[] = {4, 6, 8, 10, 12, 14};
     for (int n = 0; n <= PQ_MAX_N && rc == PQ_OK; ++n) {
-        if (!present[n])
+        if (by_n[n].empty())
             continue;
-        int best_c = 10;
+        int incumbent = P->class_log2[n] > 0 ? P->class_log2[n] : tune_get(n);
+        if (incumbent <= 0)
+            incumbent = 10;
+        pq_plan* T = plan_new();
+        if (!T) {
+            rc = fail(PQ_ERR_NOMEM, "host allocation failed");
+            break;
+        }
+        T->kind = P->kind;
+        T->opts = P->opts;
+        T->opts.method = PQ_METHOD_BATCHED;
+        T->opts.use_graph = 0;
+        T->opts.chunk_log2 = 0;
+        T->device = P->device;
+        T->num_sms = P->num_sms;
+        T->items = by_n[n];
+        T->class_log2.assign(PQ_MAX_N + 1, 0);
+        int best_c = incumbent;
         float best_t = 1e30f;
+        T->class_log2[n] = incumbent;
+        rc = schedule_and_upload(T);
+        if (rc == PQ_OK)
+            rc = time_plan(T, best_t);
         for (int cnd : cands) {
-            P->class_log2[n] = cnd;
+            if (rc != PQ_OK || cnd == incumbent)
+                continue;
+            T->class_log2[n] = cnd;
             float t = 0.0f;
-            rc = time_once(t);
-            if (rc != PQ_OK)
-                break;
-            if (t < best_t * 0.98f) {
+            rc = schedule_and_upload(T);
+            if (rc == PQ_OK)
+                rc = time_plan(T, t);
+            if (rc == PQ_OK && t < best_t * 0.99f) {
                 best_t = t;
                 best_c = cnd;
             }
         }
+        cudaStreamSynchronize(st);
+        free_plan_device(T);
+        plan_delete(T);
+        if (rc != PQ_OK)
+            break;
         P->class_log2[n] = best_c;
         tune_set(n, best_c);
     }
-    P->opts.chunk_log2 = saved_opt;
     if (rc == PQ_OK)
         rc = schedule_and_upload(P);
     P->bwd_ready = false;
