@@ -230,10 +230,24 @@ def test_bs_batched_workload(dev):
 
 
 def test_ragged_workload_sampled(dev, ragged_pb):
-    """Workload 4 at full size (65536 permanents, one persistent launch),
-    every 16th item checked against the oracle plus every item of n = 20."""
+    """Workload 4 at full size in the launch configuration the benchmark
+    times (one graph-captured persistent launch, chunks autotuned per size
+    class): every 16th item checked against the oracle plus every item of
+    n = 20."""
     pb = ragged_pb
-    got, plan = gpu_perms(pb, dev, use_graph=True)
+    db = api.DeviceBatch(pb, dev)
+    plan = api.Plan.for_batch(pb, method="batched", use_graph=True)
+    saved = pq.pq_tune_table_get()
+    try:
+        plan.autotune(db)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            out = api.permanent_batched(db, plan)
+            out = api.permanent_batched(db, plan)  # the replay of the captured graph
+        s.synchronize()
+    finally:
+        pq.pq_tune_table_set(saved)
+    got = out.cpu().numpy()
     assert np.isfinite(got).all()
     ns = np.array([int(pb.row_mult[pb.row_off[b]:pb.row_off[b] + pb.k[b]].sum())
                    for b in range(pb.batch)])
