@@ -568,7 +568,17 @@ def extra_measurements(args, dev, stream, flush, peak_tflops, fp64_lane_ops):
     t0 = time.perf_counter()
     api.bs_sample(Us, s8, order, unif)
     secs = time.perf_counter() - t0
-    res["sampler_m16_n8"] = {"samples": 2000, "s": secs, "samples_per_s": 2000 / secs}
+    # the same draws through a plan made once: each run is the upload, the
+    # 8 steps' launches and the read-back
+    splan = api.SamplerPlan(16, s8, 2000)
+    splan.run(Us, order, unif)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        splan.run(Us, order, unif)
+    secs_p = (time.perf_counter() - t0) / 5
+    splan.close()
+    res["sampler_m16_n8"] = {"samples": 2000, "s": secs, "samples_per_s": 2000 / secs,
+                             "s_planned": secs_p, "samples_per_s_planned": 2000 / secs_p}
     # a larger sampler run: m = 40 Haar, 20 photons in modes 0..19, 100 samples
     # (the last steps evaluate 20 minors of size 19, 2^18 terms each, per sample)
     U40 = torch.from_numpy(W.haar_unitary(40, W.rng_for(7, 1))).to(dev)
@@ -579,7 +589,14 @@ def extra_measurements(args, dev, stream, flush, peak_tflops, fp64_lane_ops):
     t0 = time.perf_counter()
     api.bs_sample(U40, s20, order20, unif20)
     secs = time.perf_counter() - t0
-    res["sampler_m40_n20"] = {"samples": 100, "s": secs, "samples_per_s": 100 / secs}
+    splan = api.SamplerPlan(40, s20, 100)
+    splan.run(U40, order20, unif20)
+    t0 = time.perf_counter()
+    splan.run(U40, order20, unif20)
+    secs_p = time.perf_counter() - t0
+    splan.close()
+    res["sampler_m40_n20"] = {"samples": 100, "s": secs, "samples_per_s": 100 / secs,
+                              "s_planned": secs_p, "samples_per_s_planned": 100 / secs_p}
     # lossy boson sampling (Sec. 3.2.4): m = 10 Haar factors V, W, transmissions
     # eta ~ U[0.5, 0.95], 5 photons in modes 0..4, every output pattern with at
     # most 5 photons (3003 patterns, 42504 permanents of the 20-mode dilation);
@@ -592,8 +609,12 @@ def extra_measurements(args, dev, stream, flush, peak_tflops, fp64_lane_ops):
     tl = np.concatenate([W.compositions(k, 10) for k in range(6)])
     Vd, Wd, etad = (torch.from_numpy(x).to(dev) for x in (Vl, Wl, etal))
     ms = timed(lambda: api.bs_probs_lossy(Vd, etad, Wd, sl, tl, stream=stream), 3)
+    lplan = api.LossyPlan(10, sl, tl)  # the same, planned once: each run is three launches
+    ms_p = timed(lambda: lplan.run(Vd, etad, Wd, stream=stream), 5)
+    lplan.close()
     res["lossy_m10_n5"] = {"patterns": int(tl.shape[0]), "permanents": 42504, "ms": ms,
-                           "patterns_per_s": tl.shape[0] / ms * 1e3}
+                           "patterns_per_s": tl.shape[0] / ms * 1e3, "ms_planned": ms_p,
+                           "patterns_per_s_planned": tl.shape[0] / ms_p * 1e3}
     # batched boson sampling, m = 24, 4096 patterns
     U, s, t = W.bs_batched()
     Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))

@@ -245,6 +245,22 @@ int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c128* W, int
                       const int32_t* input_occ, const int32_t* output_occ, int64_t B,
                       double* probs, void* stream);
 
+/* Planned lossy probabilities, for callers that evaluate the same patterns
+ * for many interferometers: pq_lossy_plan_create does the host work of
+ * pq_bs_probs_lossy once for input_occ (host, m) and output_occ (host, B x m)
+ * -- every loss pattern of every output, the permanents' plan, the device
+ * workspace -- and pq_lossy_plan_run evaluates probs (device, B doubles) for
+ * V, eta, W (device, as for pq_bs_probs_lossy) with three launches on
+ * `stream`: no host work, no allocation, no synchronisation.  One plan serves
+ * one stream at a time; pq_lossy_plan_destroy synchronises the device and
+ * frees it.  Errors as for pq_bs_probs_lossy; PQ_ERR_ARG for a null plan. */
+typedef struct pq_lossy_plan pq_lossy_plan;
+int pq_lossy_plan_create(int32_t m, const int32_t* input_occ, const int32_t* output_occ, int64_t B,
+                         pq_lossy_plan** out);
+int pq_lossy_plan_run(pq_lossy_plan* plan, const pq_c128* V, const double* eta, const pq_c128* W,
+                      double* probs, void* stream);
+int pq_lossy_plan_destroy(pq_lossy_plan* plan);
+
 /* Boson sampling by Clifford and Clifford's "Algorithm A", the sampler the
  * paper uses with its permanents (Sec. 4.2): photons are drawn one at a time;
  * at step k every candidate output mode i is weighted by
@@ -261,6 +277,24 @@ int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c128* W, int
  * [0, 1), all weights zero), PQ_ERR_UNSUPPORTED, PQ_ERR_NOMEM, PQ_ERR_CUDA. */
 int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_occ, int64_t nsamples,
                  const int32_t* col_order, const double* uniforms, int32_t* samples, void* stream);
+
+/* Planned sampler, for callers that draw batch after batch from interferometers
+ * with the same input occupation: pq_sampler_plan_create does the host work of
+ * pq_bs_sample once for m, input_occ (host, m) and nsamples -- the plans of the
+ * n - 1 steps' minors (nsamples x k minors of size k - 1 at step k) and the
+ * device workspace -- and pq_sampler_plan_run draws nsamples samples for U
+ * (device) with col_order, uniforms and samples as for pq_bs_sample: it uploads
+ * the draws, launches the steps on `stream`, reads the drawn modes back and
+ * synchronises `stream`; it allocates nothing.  The same U, orders and
+ * uniforms give the samples of pq_bs_sample.  One plan serves one stream at a
+ * time; pq_sampler_plan_destroy synchronises the device and frees it.  Errors
+ * as for pq_bs_sample; PQ_ERR_ARG for a null plan. */
+typedef struct pq_sampler_plan pq_sampler_plan;
+int pq_sampler_plan_create(int32_t m, const int32_t* input_occ, int64_t nsamples,
+                           pq_sampler_plan** out);
+int pq_sampler_plan_run(pq_sampler_plan* plan, const pq_c128* U, const int32_t* col_order,
+                        const double* uniforms, int32_t* samples, void* stream);
+int pq_sampler_plan_destroy(pq_sampler_plan* plan);
 
 /* Hafnians with repeated indices (Sec. 4.1, Eq. (haf_def); the paper's
  * hafnian benchmark repeats every index twice).  Item b is the hafnian of the
@@ -320,10 +354,14 @@ int pq_loop_hafnian_repeated(const pq_c128* mats, const pq_c128* gamma, const in
                              int64_t batch, pq_c128* out, void* stream);
 
 /* Times trial launches of the plan's batched kernel for each size class on
- * the given data and stores the fastest chunk length per class in the plan
- * (and in the process-wide tuning table used by later plans).  Synchronises
- * `stream`.  b is the batch the plan was made for (device descriptor); for a
- * boson-sampling plan pass b = NULL and U (device) instead. */
+ * the given data and picks the fastest chunk length per class; then times the
+ * whole batch with those picks and with the chunking the plan had, and keeps
+ * the picks -- in the plan and in the process-wide tuning table used by later
+ * plans -- only if they are at least 1% faster.  Otherwise the plan and the
+ * table stay as they were.  Synchronises `stream`.  b is the batch the plan
+ * was made for (device descriptor); for a boson-sampling plan pass b = NULL
+ * and U (device) instead.  If re-planning fails (PQ_ERR_NOMEM, PQ_ERR_CUDA)
+ * and the plan cannot be restored, later runs of it return PQ_ERR_STATE. */
 int pq_autotune(pq_plan* plan, const pq_batch* b, const pq_c128* U, void* stream);
 
 /* The process-wide tuning table: entry n (n = 0 .. PQ_MAX_N) is the Gray-code

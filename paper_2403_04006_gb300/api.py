@@ -352,6 +352,38 @@ def bs_probs_lossy(V: torch.Tensor, eta: torch.Tensor, W: torch.Tensor, s, t,
     return probs
 
 
+class LossyPlan:
+    """Lossy detection probabilities of fixed patterns (pq_lossy_plan_*):
+    planned once for input occupation ``s`` and output patterns ``t`` (host
+    arrays), ``run`` evaluates them for an interferometer V diag(sqrt(eta)) W
+    without host work, allocation or synchronisation."""
+
+    def __init__(self, m: int, s, t):
+        t = np.atleast_2d(np.asarray(t, dtype=np.int32))
+        self.m, self.count = int(m), int(t.shape[0])
+        self.handle = _pq.pq_lossy_plan_create(self.m, np.asarray(s), t)
+
+    def run(self, V: torch.Tensor, eta: torch.Tensor, W: torch.Tensor,
+            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.count, dtype=torch.float64, device=V.device)
+        Vc, etac, Wc = V.contiguous(), eta.contiguous(), W.contiguous()
+        _pq.pq_lossy_plan_run(self.handle, _ptr(Vc), _ptr(etac), _ptr(Wc),
+                              _ptr(out) if self.count else None, _stream_handle(stream))
+        return out
+
+    def close(self):
+        if self.handle:
+            _pq.pq_lossy_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def bs_sample(U: torch.Tensor, s, col_order, uniforms, stream=None) -> np.ndarray:
     """Boson-sampling outputs by Algorithm A (pq_bs_sample): U on the GPU,
     input occupation s, and the run's random column orders and uniforms
@@ -359,6 +391,38 @@ def bs_sample(U: torch.Tensor, s, col_order, uniforms, stream=None) -> np.ndarra
     Uc = U.contiguous()
     return _pq.pq_bs_sample(_ptr(Uc), U.shape[0], np.asarray(s), col_order,
                             uniforms, _stream_handle(stream))
+
+
+class SamplerPlan:
+    """Algorithm A with the host work done once (pq_sampler_plan_*): planned
+    for m modes, input occupation ``s`` and ``nsamples`` draws per run; ``run``
+    takes U on the GPU and the run's column orders and uniforms (host arrays,
+    nsamples x n) and returns nsamples x m occupations, the samples that
+    ``bs_sample`` gives for the same arguments."""
+
+    def __init__(self, m: int, s, nsamples: int):
+        self.m, self.nsamples = int(m), int(nsamples)
+        self.handle = _pq.pq_sampler_plan_create(self.m, np.asarray(s), self.nsamples)
+
+    def run(self, U: torch.Tensor, col_order, uniforms, stream=None) -> np.ndarray:
+        col_order = np.asarray(col_order, dtype=np.int32)
+        uniforms = np.asarray(uniforms, dtype=np.float64)
+        if col_order.shape[0] != self.nsamples or uniforms.shape != col_order.shape:
+            raise ValueError("col_order and uniforms must be nsamples x n")
+        Uc = U.contiguous()
+        return _pq.pq_sampler_plan_run(self.handle, _ptr(Uc), self.m, col_order, uniforms,
+                                       _stream_handle(stream))
+
+    def close(self):
+        if self.handle:
+            _pq.pq_sampler_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hafnian_repeated(mats: torch.Tensor, mat_off, k, rep, rep_off, gamma: torch.Tensor | None = None,

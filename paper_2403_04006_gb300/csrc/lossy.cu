@@ -82,13 +82,39 @@ static void compositions(int k, int m, std::vector<int32_t>& cur, int pos,
 
 }  // namespace pqi
 
-using namespace pqi;
+// A planned lossy batch: the 2m-mode boson-sampling plan of every (t, u)
+// pattern, the pattern offsets of each t and the device workspace.
+struct pq_lossy_plan {
+    int32_t m = 0;
+    int64_t B = 0, NB = 0;
+    pq_plan* P = nullptr;
+    double2* Ubig = nullptr;     // 2m x 2m
+    double* pbig = nullptr;      // NB probabilities of the (t, u) patterns
+    int64_t* first_d = nullptr;  // B + 1 offsets of each t's patterns
+};
 
-extern "C" int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c128* W, int32_t m,
-                                 const int32_t* input_occ, const int32_t* output_occ, int64_t B,
-                                 double* probs, void* stream)
+namespace pqi {
+
+static void lossy_plan_free(pq_lossy_plan* L)
 {
-    if (!V || !eta || !W || !input_occ || (B > 0 && (!output_occ || !probs)))
+    if (!L)
+        return;
+    if (L->P)
+        pq_plan_destroy(L->P);
+    dev_free(L->Ubig);
+    dev_free(L->pbig);
+    dev_free(L->first_d);
+    delete L;
+    host_object_freed();
+}
+
+// Host planning: expand every output pattern t into its loss patterns u,
+// plan the permanents, allocate and upload.  Synchronous.
+static int lossy_plan_build(int32_t m, const int32_t* input_occ, const int32_t* output_occ,
+                            int64_t B, pq_lossy_plan** out)
+{
+    *out = nullptr;
+    if (!input_occ || (B > 0 && !output_occ))
         return report(PQ_ERR_ARG, "null argument");
     if (m <= 0 || 2 * m > PQ_MAX_DIM || B < 0)
         return report(m <= 0 || B < 0 ? PQ_ERR_ARG : PQ_ERR_UNSUPPORTED,
@@ -122,47 +148,107 @@ extern "C" int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c
         if (first[b + 1] > (int64_t(1) << 28))
             return report(PQ_ERR_UNSUPPORTED, "too many loss patterns");
     }
-    const int64_t NB = first[B];
+    if (!host_object_alloc_ok())
+        return report(PQ_ERR_NOMEM, "host allocation failed");
+    pq_lossy_plan* L = new (std::nothrow) pq_lossy_plan();
+    if (!L) {
+        host_object_freed();
+        return report(PQ_ERR_NOMEM, "host allocation failed");
+    }
+    L->m = m;
+    L->B = B;
+    L->NB = first[B];
+    if (B == 0) {
+        *out = L;
+        return PQ_OK;
+    }
     std::vector<int32_t> sbig(2 * m, 0);
     for (int j = 0; j < m; ++j)
         sbig[j] = input_occ[j];
-    if (B == 0)
+    int rc = pq_plan_create_bs(2 * m, sbig.data(), big_t.data(), L->NB, nullptr, &L->P);
+    if (rc == PQ_OK &&
+        (dev_alloc((void**)&L->Ubig, sizeof(double2) * 4 * m * m) != cudaSuccess ||
+         dev_alloc((void**)&L->pbig, sizeof(double) * L->NB) != cudaSuccess ||
+         dev_alloc((void**)&L->first_d, sizeof(int64_t) * (B + 1)) != cudaSuccess))
+        rc = report(PQ_ERR_NOMEM, "lossy workspace allocation failed");
+    if (rc == PQ_OK && cudaMemcpy(L->first_d, first.data(), sizeof(int64_t) * (B + 1),
+                                  cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = report(PQ_ERR_CUDA, "pattern offsets upload failed");
+    if (rc != PQ_OK) {
+        lossy_plan_free(L);
+        return rc;
+    }
+    *out = L;
+    return PQ_OK;
+}
+
+// The dilation, the permanents of every (t, u) and the marginals, on stream;
+// no allocation, no host access, no synchronisation.
+static int lossy_plan_launch(pq_lossy_plan* L, const pq_c128* V, const double* eta,
+                             const pq_c128* W, double* probs, cudaStream_t st)
+{
+    if (!V || !eta || !W || (L->B > 0 && !probs))
+        return report(PQ_ERR_ARG, "null argument");
+    if (L->B == 0)
         return PQ_OK;
-    pq_plan* P = nullptr;
-    int rc = pq_plan_create_bs(2 * m, sbig.data(), big_t.data(), NB, nullptr, &P);
+    const int m = L->m;
+    lossy_dilation_kernel<<<(4 * m * m + 255) / 256, 256, 0, st>>>(
+        reinterpret_cast<const double2*>(V), eta, reinterpret_cast<const double2*>(W), m, L->Ubig);
+    if (cudaGetLastError() != cudaSuccess)
+        return report(PQ_ERR_CUDA, "dilation kernel failed");
+    int rc = plan_run_forward(L->P, L->Ubig, nullptr, L->pbig, st);
+    if (rc != PQ_OK)
+        return rc;
+    const unsigned blocks = (unsigned)((L->B + 127) / 128 < 4096 ? (L->B + 127) / 128 : 4096);
+    lossy_marginal_kernel<<<blocks, 128, 0, st>>>(L->pbig, L->first_d, L->B, probs);
+    if (cudaGetLastError() != cudaSuccess)
+        return report(PQ_ERR_CUDA, "lossy marginal failed");
+    return PQ_OK;
+}
+
+}  // namespace pqi
+
+using namespace pqi;
+
+extern "C" int pq_lossy_plan_create(int32_t m, const int32_t* input_occ, const int32_t* output_occ,
+                                    int64_t B, pq_lossy_plan** out)
+{
+    if (!out)
+        return report(PQ_ERR_ARG, "null argument");
+    return lossy_plan_build(m, input_occ, output_occ, B, out);
+}
+
+extern "C" int pq_lossy_plan_run(pq_lossy_plan* plan, const pq_c128* V, const double* eta,
+                                 const pq_c128* W, double* probs, void* stream)
+{
+    if (!plan)
+        return report(PQ_ERR_ARG, "null plan");
+    return lossy_plan_launch(plan, V, eta, W, probs, (cudaStream_t)stream);
+}
+
+extern "C" int pq_lossy_plan_destroy(pq_lossy_plan* plan)
+{
+    if (plan) {
+        cudaDeviceSynchronize();
+        lossy_plan_free(plan);
+    }
+    return PQ_OK;
+}
+
+extern "C" int pq_bs_probs_lossy(const pq_c128* V, const double* eta, const pq_c128* W, int32_t m,
+                                 const int32_t* input_occ, const int32_t* output_occ, int64_t B,
+                                 double* probs, void* stream)
+{
+    if (!V || !eta || !W || !input_occ || (B > 0 && (!output_occ || !probs)))
+        return report(PQ_ERR_ARG, "null argument");
+    pq_lossy_plan* L = nullptr;
+    int rc = lossy_plan_build(m, input_occ, output_occ, B, &L);
     if (rc != PQ_OK)
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    double2* Ubig = nullptr;
-    double* pbig = nullptr;
-    int64_t* first_d = nullptr;
-    if (dev_alloc((void**)&Ubig, sizeof(double2) * 4 * m * m) != cudaSuccess ||
-        dev_alloc((void**)&pbig, sizeof(double) * NB) != cudaSuccess ||
-        dev_alloc((void**)&first_d, sizeof(int64_t) * (B + 1)) != cudaSuccess) {
-        rc = report(PQ_ERR_NOMEM, "lossy workspace allocation failed");
-    }
-    if (rc == PQ_OK &&
-        cudaMemcpyAsync(first_d, first.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice,
-                        st) != cudaSuccess)
-        rc = report(PQ_ERR_CUDA, "pattern offsets upload failed");
-    if (rc == PQ_OK) {
-        lossy_dilation_kernel<<<(4 * m * m + 255) / 256, 256, 0, st>>>(
-            reinterpret_cast<const double2*>(V), eta, reinterpret_cast<const double2*>(W), m,
-            Ubig);
-        if (cudaGetLastError() != cudaSuccess)
-            rc = report(PQ_ERR_CUDA, "dilation kernel failed");
-    }
-    if (rc == PQ_OK)
-        rc = plan_run_forward(P, Ubig, nullptr, pbig, st);
-    if (rc == PQ_OK) {
-        const unsigned blocks = (unsigned)((B + 127) / 128 < 4096 ? (B + 127) / 128 : 4096);
-        lossy_marginal_kernel<<<blocks, 128, 0, st>>>(pbig, first_d, B, probs);
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
-            rc = report(PQ_ERR_CUDA, "lossy marginal failed");
-    }
-    dev_free(Ubig);
-    dev_free(pbig);
-    dev_free(first_d);
-    pq_plan_destroy(P);
+    rc = lossy_plan_launch(L, V, eta, W, probs, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == PQ_OK)
+        rc = report(PQ_ERR_CUDA, "lossy probabilities failed");
+    lossy_plan_free(L);
     return rc;
 }

@@ -325,7 +325,9 @@ static double bwd_instr_per_term(const ItemPlan& it)
     return 4.0 * l + 4.0 * std::max(l - 2, 0) + 8.0 * std::max(l - 2, 0) + 6.0 + rep;
 }
 
-static int default_log2_for(const pq_plan* P, const ItemPlan& it)
+// The chunk log2 that the caller fixed for this permanent (plan option,
+// autotuned class, process-wide table), or 0 if none did.
+static int explicit_log2_for(const pq_plan* P, const ItemPlan& it)
 {
     if (P->opts.chunk_log2 > 0)
         return P->opts.chunk_log2;
@@ -335,10 +337,13 @@ static int default_log2_for(const pq_plan* P, const ItemPlan& it)
     if (P->opts.shard_count == 0 && it.n >= 0 && it.n < (int)P->class_log2.size() &&
         P->class_log2[it.n] > 0)
         return P->class_log2[it.n];
-    int tuned = tune_get(it.n);
-    if (tuned > 0)
-        return tuned;
-    return 10;
+    return tune_get(it.n);
+}
+
+static int default_log2_for(const pq_plan* P, const ItemPlan& it)
+{
+    const int e = explicit_log2_for(P, it);
+    return e > 0 ? e : 10;
 }
 
 template <typename T>
@@ -397,6 +402,11 @@ static void free_plan_device(pq_plan* P)
 // Chunks, tasks, descriptors, device upload.
 static int schedule_and_upload(pq_plan* P)
 {
+    P->uploaded = false;
+    if (P->graph) {  // it holds the old buffers' addresses
+        cudaGraphExecDestroy(P->graph);
+        P->graph = nullptr;
+    }
     const int64_t np = (int64_t)P->items.size();
     P->nperm = np;
     int lmax_needed = 1, kmax = 1;
@@ -415,12 +425,57 @@ static int schedule_and_upload(pq_plan* P)
     // fills the GPU with many permanents at once.
     const int64_t plain_min = (int64_t)P->num_sms * 4 * kWarp;
     const int64_t plain_max = (int64_t)P->num_sms * 16 * 2 * kWarp;
-    for (ItemPlan& it : P->items) {
-        const int64_t plain_chunks = std::max(plain_min, std::min(plain_max, it.T / 64));
-        choose_chunks(it, default_log2_for(P, it), kMaxLowDigits,
-                      (P->opts.method == PQ_METHOD_PLAIN && P->opts.chunk_log2 == 0)
-                          ? plain_chunks
-                          : kWarp);
+
+    // launch geometry (it fixes the resident warps the batched cut is balanced for)
+    const int per_warp = fwd_smem_per_warp(P->kmax, P->lmax);
+    if (per_warp > 200 * 1024)
+        return fail(PQ_ERR_UNSUPPORTED, "shared memory per warp %d too large", per_warp);
+    int wpb = 0, bps = 0;
+    launch_geometry(fwd_regs_per_thread(P->lmax), per_warp,
+                    P->opts.warps_per_block > 0 ? P->opts.warps_per_block : 8,
+                    P->opts.blocks_per_sm > 0 ? P->opts.blocks_per_sm : 8, wpb, bps);
+    P->wpb = wpb;
+    P->blocks = std::max(1, P->num_sms * bps);
+
+    if (P->opts.method == PQ_METHOD_PLAIN) {
+        for (ItemPlan& it : P->items) {
+            const int64_t plain_chunks = std::max(plain_min, std::min(plain_max, it.T / 64));
+            choose_chunks(it, default_log2_for(P, it), kMaxLowDigits,
+                          P->opts.chunk_log2 == 0 ? plain_chunks : kWarp);
+        }
+    } else {
+        // The batched method cuts each permanent into at least a warp's worth
+        // of chunks.  A small batch then has too few, too long tasks for the
+        // GPU: the last ones leave SMs idle (4096 permanents of the ragged
+        // recipe took 4.0 ms with chunks of up to 2^10 terms, 1.5 ms with 2^6).
+        // So the chunk cap is lowered, for the whole batch, until the longest
+        // warp task is at most half of a resident warp's average share of the
+        // work; large batches keep their caps (65536 permanents: the longest
+        // task is a quarter of a share).  Chunk lengths that the caller fixed
+        // are kept as they are.
+        const double warps = (double)P->blocks * P->wpb;
+        auto cut_all = [&](int gcap) {
+            double total = 0.0, longest = 0.0;
+            for (ItemPlan& it : P->items) {
+                const int e = explicit_log2_for(P, it);
+                choose_chunks(it, e > 0 ? e : std::min(10, gcap), kMaxLowDigits, kWarp);
+                if (it.trivial)
+                    continue;
+                const double cost = (double)it.L * fwd_flops_per_term(it) +
+                                    2.0 * (double)((int)it.drow.size() - it.J) * it.l + 2.0 * it.l;
+                total += cost * (double)((it.nchunks + kWarp - 1) / kWarp);
+                longest = std::max(longest, cost);
+            }
+            return total > 0.0 ? longest / (total / warps) : 0.0;
+        };
+        int gcap = 30;
+        double ratio = cut_all(gcap);
+        if (P->opts.chunk_log2 == 0 && P->opts.shard_count == 0) {
+            for (int c = 12; c >= 4 && ratio > 0.5; --c) {
+                gcap = c;
+                ratio = cut_all(gcap);
+            }
+        }
     }
 
     P->desc_h.assign(np, PermDesc{});
@@ -523,17 +578,6 @@ static int schedule_and_upload(pq_plan* P)
     for (size_t q = 0; q < order.size(); ++q)
         P->tasks_batched_h[q] = P->tasks_plain_h[order[q]];
 
-    // launch geometry
-    const int per_warp = fwd_smem_per_warp(P->kmax, P->lmax);
-    if (per_warp > 200 * 1024)
-        return fail(PQ_ERR_UNSUPPORTED, "shared memory per warp %d too large", per_warp);
-    int wpb = 0, bps = 0;
-    launch_geometry(fwd_regs_per_thread(P->lmax), per_warp,
-                    P->opts.warps_per_block > 0 ? P->opts.warps_per_block : 8,
-                    P->opts.blocks_per_sm > 0 ? P->opts.blocks_per_sm : 8, wpb, bps);
-    P->wpb = wpb;
-    P->blocks = std::max(1, P->num_sms * bps);
-
     P->stats.permanents = np;
     P->stats.terms = terms;
     P->stats.flops_forward = flops_f;
@@ -569,10 +613,7 @@ static int schedule_and_upload(pq_plan* P)
     cudaError_t e = fwd_prepare(P->lmax, P->wpb * per_warp);
     if (e != cudaSuccess)
         return fail(PQ_ERR_CUDA, "kernel attribute setup failed: %s", cudaGetErrorString(e));
-    if (P->graph) {
-        cudaGraphExecDestroy(P->graph);
-        P->graph = nullptr;
-    }
+    P->uploaded = true;
     return PQ_OK;
 }
 
@@ -796,6 +837,8 @@ static ExecArgs exec_args(pq_plan* P, const void* src, void* amps, double* probs
 static int run_forward_raw(pq_plan* P, const void* src, void* amps, double* probs,
                            cudaStream_t st, double* partial = nullptr)
 {
+    if (!P->uploaded)
+        return fail(PQ_ERR_STATE, "the plan lost its device data in a failed re-planning");
     PQ_CUDA(cudaMemsetAsync(P->counters_d, 0, (size_t)(P->nperm + 1) * sizeof(int32_t), st));
     if (P->nperm == 0)
         return PQ_OK;
@@ -1296,6 +1339,8 @@ static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, co
 {
     if (P->opts.shard_count > 0)
         return fail(PQ_ERR_UNSUPPORTED, "the backward does not run on a sharded plan");
+    if (!P->uploaded)
+        return fail(PQ_ERR_STATE, "the plan lost its device data in a failed re-planning");
     int rc = ensure_backward(P);
     if (rc != PQ_OK)
         return rc;
@@ -1473,7 +1518,8 @@ extern "C" int pq_clements_backward(const double* theta, const double* phi, int3
 // 2^14 terms, and keep a candidate only if it is at least 1% faster than the
 // incumbent.  Timing each class on its own matters: a small class changes
 // the whole batch's time by less than the timing noise, and a choice made
-// from whole-batch times can then only be noise.
+// from whole-batch times can then only be noise.  The picks are then checked
+// once on the whole batch against the plan's previous chunking.
 extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void* stream)
 {
     if (!P)
@@ -1527,6 +1573,7 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
         return PQ_OK;
     };
     const int cands[] = {4, 6, 8, 10, 12, 14};
+    const std::vector<int32_t> saved_class = P->class_log2;
     for (int n = 0; n <= PQ_MAX_N && rc == PQ_OK; ++n) {
         if (by_n[n].empty())
             continue;
@@ -1572,10 +1619,35 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
         if (rc != PQ_OK)
             break;
         P->class_log2[n] = best_c;
-        tune_set(n, best_c);
     }
-    if (rc == PQ_OK)
+    // The classes were timed alone.  In the whole batch the chunking the plan
+    // had before (for a small batch, caps lowered so that the warp tasks
+    // balance over the GPU) can be the faster one: time the batch both ways
+    // and keep the per-class choice only if it is at least 1% faster.
+    if (rc == PQ_OK) {
+        const std::vector<int32_t> picks = P->class_log2;
+        float t_picks = 0.0f, t_before = 0.0f;
         rc = schedule_and_upload(P);
+        if (rc == PQ_OK)
+            rc = time_plan(P, t_picks);
+        if (rc == PQ_OK) {
+            P->class_log2 = saved_class;
+            rc = schedule_and_upload(P);
+            if (rc == PQ_OK)
+                rc = time_plan(P, t_before);
+        }
+        if (rc == PQ_OK && t_picks < 0.99f * t_before) {
+            P->class_log2 = picks;
+            for (int n = 0; n <= PQ_MAX_N; ++n)
+                if (!by_n[n].empty())
+                    tune_set(n, picks[n]);
+            rc = schedule_and_upload(P);
+        }
+    }
+    if (rc != PQ_OK && !P->uploaded) {  // try to leave the plan as it was
+        P->class_log2 = saved_class;
+        schedule_and_upload(P);
+    }
     P->bwd_ready = false;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -81,6 +81,7 @@ struct pq_plan {
     int32_t* err_d = nullptr;
     // backward schedule and workspace (built on the first backward call)
     bool bwd_ready = false;
+    bool uploaded = false;  // device data matches the host schedule (a failed re-plan clears it)
     std::vector<pqi::PermDesc> desc_bwd_h;
     std::vector<pqi::Task> tasks_bwd_plain_h, tasks_bwd_batched_h;
     std::vector<int64_t> plain_first_bwd;

@@ -109,18 +109,50 @@ __global__ void sampler_step_kernel(const double2* U, int m, int n, int k, int64
 
 }  // namespace pqi
 
-using namespace pqi;
+// A planned sampler: the plan of every step's minors (made once, by host
+// threads side by side), the photon columns' input modes and the device
+// workspace.  A run uploads the draws, runs the steps and reads the samples.
+struct pq_sampler_plan {
+    int32_t m = 0, n = 0;
+    int64_t nsamples = 0;
+    std::vector<int32_t> modes;   // input mode of each photon column
+    std::vector<pq_plan*> plans;  // index k = 2 .. n
+    double2 *mats_d = nullptr, *per_d = nullptr;
+    double *w_d = nullptr, *u_d = nullptr;
+    int32_t *cols_d = nullptr, *drawn_d = nullptr, *err_d = nullptr;
+    std::vector<int32_t> cols_h, drawn_h;  // host staging of one run
+};
 
-extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_occ,
-                            int64_t nsamples, const int32_t* col_order, const double* uniforms,
-                            int32_t* samples, void* stream)
+namespace pqi {
+
+static void sampler_plan_free(pq_sampler_plan* S)
 {
-    if (!U || !input_occ || (nsamples > 0 && (!col_order || !uniforms || !samples)))
+    if (!S)
+        return;
+    for (pq_plan* P : S->plans)
+        if (P)
+            pq_plan_destroy(P);
+    dev_free(S->mats_d);
+    dev_free(S->per_d);
+    dev_free(S->w_d);
+    dev_free(S->u_d);
+    dev_free(S->cols_d);
+    dev_free(S->drawn_d);
+    dev_free(S->err_d);
+    delete S;
+    host_object_freed();
+}
+
+static int sampler_plan_build(int32_t m, const int32_t* input_occ, int64_t nsamples,
+                              pq_sampler_plan** out)
+{
+    *out = nullptr;
+    if (!input_occ)
         return report(PQ_ERR_ARG, "null argument");
     if (m <= 0 || m > PQ_MAX_DIM || nsamples < 0)
         return report(PQ_ERR_ARG, "bad sizes");
     int n = 0;
-    std::vector<int32_t> modes;  // input mode of each photon column
+    std::vector<int32_t> modes;
     for (int j = 0; j < m; ++j) {
         if (input_occ[j] < 0)
             return report(PQ_ERR_ARG, "negative input occupation");
@@ -130,37 +162,36 @@ extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_oc
     }
     if (n > PQ_MAX_N)
         return report(PQ_ERR_UNSUPPORTED, "too many photons");
-    std::vector<int32_t> cols((size_t)nsamples * n);
-    for (int64_t b = 0; b < nsamples; ++b) {  // every column order is a permutation
-        std::vector<char> seen(n, 0);
-        for (int q = 0; q < n; ++q) {
-            const int32_t c = col_order[b * n + q];
-            if (c < 0 || c >= n || seen[c])
-                return report(PQ_ERR_ARG, "col_order row is not a permutation of 0 .. n-1");
-            seen[c] = 1;
-            cols[(size_t)b * n + q] = modes[c];
-        }
-    }
-    for (int64_t b = 0; b < nsamples * n; ++b)
-        if (!(uniforms[b] >= 0.0 && uniforms[b] < 1.0))
-            return report(PQ_ERR_ARG, "uniforms must lie in [0, 1)");
-    for (int64_t e = 0; e < nsamples * m; ++e)
-        samples[e] = 0;
-    if (nsamples == 0 || n == 0)
-        return PQ_OK;
-    if (nsamples > (int64_t(1) << 40) / ((int64_t)n * n * n + m))
+    if (n > 0 && nsamples > (int64_t(1) << 40) / ((int64_t)n * n * n + m))
         return report(PQ_ERR_UNSUPPORTED, "sampler workspace too large");
+    if (!host_object_alloc_ok())
+        return report(PQ_ERR_NOMEM, "host allocation failed");
+    pq_sampler_plan* S = new (std::nothrow) pq_sampler_plan();
+    if (!S) {
+        host_object_freed();
+        return report(PQ_ERR_NOMEM, "host allocation failed");
+    }
+    S->m = m;
+    S->n = n;
+    S->nsamples = nsamples;
+    S->modes = modes;
+    S->plans.assign(n + 1, nullptr);
+    if (nsamples == 0 || n == 0) {
+        *out = S;
+        return PQ_OK;
+    }
 
     // one plan per step k >= 2: nsamples * k minors of size k - 1, every
     // multiplicity one, item (b, j) at element offset (b k + j) (k-1)^2.  The
     // plans are independent, so host threads build them side by side.
-    std::vector<pq_plan*> plans(n + 1, nullptr);
     std::vector<int> prc(n + 1, PQ_OK);
     std::vector<std::string> perr(n + 1);
     std::atomic<int> next_k(2);
     int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess)
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        sampler_plan_free(S);
         return report(PQ_ERR_CUDA, "no current CUDA device");
+    }
     auto worker = [&]() {
         cudaSetDevice(device);  // a new host thread starts on device 0
         for (int k = next_k++; k <= n; k = next_k++) {
@@ -179,7 +210,7 @@ extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_oc
             sz.row_off = zero_off.data();
             sz.col_mult = ones.data();
             sz.col_off = zero_off.data();
-            prc[k] = pq_plan_create(&sz, nullptr, &plans[k]);
+            prc[k] = pq_plan_create(&sz, nullptr, &S->plans[k]);
             if (prc[k] != PQ_OK)
                 perr[k] = pq_last_error();
         }
@@ -200,79 +231,146 @@ extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_oc
     // Plans made side by side may have raised the kernel's shared-memory
     // limit out of order: raise it once more for each, in turn.
     for (int k = 2; k <= n && rc == PQ_OK; ++k)
-        if (plan_prepare_forward(plans[k]) != PQ_OK)
+        if (plan_prepare_forward(S->plans[k]) != PQ_OK)
             rc = report(PQ_ERR_CUDA, "kernel attribute setup failed");
-    cudaStream_t st = (cudaStream_t)stream;
     const int64_t Bmax = nsamples * n;
     const int64_t mat_elems = std::max<int64_t>(1, nsamples * n * (int64_t)(n - 1) * (n - 1));
-    double2 *mats_d = nullptr, *per_d = nullptr;
-    double *w_d = nullptr, *u_d = nullptr;
-    int32_t *cols_d = nullptr, *drawn_d = nullptr, *err_d = nullptr;
     if (rc == PQ_OK &&
-        (dev_alloc((void**)&mats_d, mat_elems * sizeof(double2)) != cudaSuccess ||
-         dev_alloc((void**)&per_d, Bmax * sizeof(double2)) != cudaSuccess ||
-         dev_alloc((void**)&w_d, nsamples * m * sizeof(double)) != cudaSuccess ||
-         dev_alloc((void**)&u_d, nsamples * n * sizeof(double)) != cudaSuccess ||
-         dev_alloc((void**)&cols_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
-         dev_alloc((void**)&drawn_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
-         dev_alloc((void**)&err_d, sizeof(int32_t)) != cudaSuccess))
+        (dev_alloc((void**)&S->mats_d, mat_elems * sizeof(double2)) != cudaSuccess ||
+         dev_alloc((void**)&S->per_d, Bmax * sizeof(double2)) != cudaSuccess ||
+         dev_alloc((void**)&S->w_d, nsamples * m * sizeof(double)) != cudaSuccess ||
+         dev_alloc((void**)&S->u_d, nsamples * n * sizeof(double)) != cudaSuccess ||
+         dev_alloc((void**)&S->cols_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
+         dev_alloc((void**)&S->drawn_d, nsamples * n * sizeof(int32_t)) != cudaSuccess ||
+         dev_alloc((void**)&S->err_d, sizeof(int32_t)) != cudaSuccess))
         rc = report(PQ_ERR_NOMEM, "sampler workspace allocation failed");
-    if (rc == PQ_OK &&
-        (cudaMemcpyAsync(u_d, uniforms, nsamples * n * sizeof(double), cudaMemcpyHostToDevice,
-                         st) != cudaSuccess ||
-         cudaMemcpyAsync(cols_d, cols.data(), nsamples * n * sizeof(int32_t),
-                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
-         cudaMemsetAsync(drawn_d, 0, nsamples * n * sizeof(int32_t), st) != cudaSuccess ||
-         cudaMemsetAsync(err_d, 0, sizeof(int32_t), st) != cudaSuccess))
+    if (rc != PQ_OK) {
+        sampler_plan_free(S);
+        return rc;
+    }
+    S->cols_h.resize((size_t)nsamples * n);
+    S->drawn_h.resize((size_t)nsamples * n);
+    *out = S;
+    return PQ_OK;
+}
+
+// One run: check and upload the draws, the steps, read the drawn modes back
+// (synchronises `st`) and count them into samples.
+static int sampler_plan_launch(pq_sampler_plan* S, const pq_c128* U, const int32_t* col_order,
+                               const double* uniforms, int32_t* samples, cudaStream_t st)
+{
+    const int m = S->m, n = S->n;
+    const int64_t nsamples = S->nsamples;
+    if (!U || (nsamples > 0 && (!col_order || !uniforms || !samples)))
+        return report(PQ_ERR_ARG, "null argument");
+    for (int64_t b = 0; b < nsamples; ++b) {  // every column order is a permutation
+        std::vector<char> seen(n, 0);
+        for (int q = 0; q < n; ++q) {
+            const int32_t c = col_order[b * n + q];
+            if (c < 0 || c >= n || seen[c])
+                return report(PQ_ERR_ARG, "col_order row is not a permutation of 0 .. n-1");
+            seen[c] = 1;
+            S->cols_h[(size_t)b * n + q] = S->modes[c];
+        }
+    }
+    for (int64_t b = 0; b < nsamples * n; ++b)
+        if (!(uniforms[b] >= 0.0 && uniforms[b] < 1.0))
+            return report(PQ_ERR_ARG, "uniforms must lie in [0, 1)");
+    for (int64_t e = 0; e < nsamples * m; ++e)
+        samples[e] = 0;
+    if (nsamples == 0 || n == 0)
+        return PQ_OK;
+    int rc = PQ_OK;
+    if (cudaMemcpyAsync(S->u_d, uniforms, nsamples * n * sizeof(double), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(S->cols_d, S->cols_h.data(), nsamples * n * sizeof(int32_t),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(S->drawn_d, 0, nsamples * n * sizeof(int32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(S->err_d, 0, sizeof(int32_t), st) != cudaSuccess)
         rc = report(PQ_ERR_CUDA, "sampler upload failed");
-    const unsigned sblocks =
-        (unsigned)std::min<int64_t>((nsamples + 127) / 128, 4096);
+    const unsigned sblocks = (unsigned)std::min<int64_t>((nsamples + 127) / 128, 4096);
     for (int k = 1; k <= n && rc == PQ_OK; ++k) {
         if (k >= 2) {
             const int64_t total = nsamples * k * (int64_t)(k - 1) * (k - 1);
             const unsigned gblocks = (unsigned)std::min<int64_t>((total + 255) / 256, 65536);
-            sampler_gather_kernel<<<gblocks, 256, 0, st>>>(
-                reinterpret_cast<const double2*>(U), m, n, k, nsamples, cols_d, drawn_d, mats_d);
+            sampler_gather_kernel<<<gblocks, 256, 0, st>>>(reinterpret_cast<const double2*>(U), m,
+                                                           n, k, nsamples, S->cols_d, S->drawn_d,
+                                                           S->mats_d);
             if (cudaGetLastError() != cudaSuccess) {
                 rc = report(PQ_ERR_CUDA, "minor gather failed");
                 break;
             }
-            rc = plan_run_forward(plans[k], mats_d, per_d, nullptr, st);
+            rc = plan_run_forward(S->plans[k], S->mats_d, S->per_d, nullptr, st);
             if (rc != PQ_OK)
                 break;
         }
         sampler_step_kernel<<<sblocks, 128, 0, st>>>(reinterpret_cast<const double2*>(U), m, n, k,
-                                                     nsamples, cols_d, per_d, u_d, w_d, drawn_d,
-                                                     err_d);
+                                                     nsamples, S->cols_d, S->per_d, S->u_d, S->w_d,
+                                                     S->drawn_d, S->err_d);
         if (cudaGetLastError() != cudaSuccess)
             rc = report(PQ_ERR_CUDA, "sampling step failed");
     }
-    std::vector<int32_t> drawn((size_t)nsamples * n);
     int32_t err = 0;
     if (rc == PQ_OK &&
-        (cudaMemcpyAsync(drawn.data(), drawn_d, nsamples * n * sizeof(int32_t),
+        (cudaMemcpyAsync(S->drawn_h.data(), S->drawn_d, nsamples * n * sizeof(int32_t),
                          cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-         cudaMemcpyAsync(&err, err_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+         cudaMemcpyAsync(&err, S->err_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
              cudaSuccess ||
          cudaStreamSynchronize(st) != cudaSuccess))
         rc = report(PQ_ERR_CUDA, "sampler read-back failed");
     if (rc == PQ_OK && err)
         rc = report(PQ_ERR_ARG, "all weights of a sampling step are zero");
-    if (rc != PQ_OK)
+    if (rc != PQ_OK) {
         cudaStreamSynchronize(st);
-    dev_free(mats_d);
-    dev_free(per_d);
-    dev_free(w_d);
-    dev_free(u_d);
-    dev_free(cols_d);
-    dev_free(drawn_d);
-    dev_free(err_d);
-    for (pq_plan* P : plans)
-        if (P)
-            pq_plan_destroy(P);
-    if (rc == PQ_OK)
-        for (int64_t b = 0; b < nsamples; ++b)
-            for (int q = 0; q < n; ++q)
-                samples[b * m + drawn[(size_t)b * n + q]] += 1;
+        return rc;
+    }
+    for (int64_t b = 0; b < nsamples; ++b)
+        for (int q = 0; q < n; ++q)
+            samples[b * m + S->drawn_h[(size_t)b * n + q]] += 1;
+    return PQ_OK;
+}
+
+}  // namespace pqi
+
+using namespace pqi;
+
+extern "C" int pq_sampler_plan_create(int32_t m, const int32_t* input_occ, int64_t nsamples,
+                                      pq_sampler_plan** out)
+{
+    if (!out)
+        return report(PQ_ERR_ARG, "null argument");
+    return sampler_plan_build(m, input_occ, nsamples, out);
+}
+
+extern "C" int pq_sampler_plan_run(pq_sampler_plan* plan, const pq_c128* U,
+                                   const int32_t* col_order, const double* uniforms,
+                                   int32_t* samples, void* stream)
+{
+    if (!plan)
+        return report(PQ_ERR_ARG, "null plan");
+    return sampler_plan_launch(plan, U, col_order, uniforms, samples, (cudaStream_t)stream);
+}
+
+extern "C" int pq_sampler_plan_destroy(pq_sampler_plan* plan)
+{
+    if (plan) {
+        cudaDeviceSynchronize();
+        sampler_plan_free(plan);
+    }
+    return PQ_OK;
+}
+
+extern "C" int pq_bs_sample(const pq_c128* U, int32_t m, const int32_t* input_occ,
+                            int64_t nsamples, const int32_t* col_order, const double* uniforms,
+                            int32_t* samples, void* stream)
+{
+    if (!U || !input_occ || (nsamples > 0 && (!col_order || !uniforms || !samples)))
+        return report(PQ_ERR_ARG, "null argument");
+    pq_sampler_plan* S = nullptr;
+    int rc = sampler_plan_build(m, input_occ, nsamples, &S);
+    if (rc != PQ_OK)
+        return rc;
+    rc = sampler_plan_launch(S, U, col_order, uniforms, samples, (cudaStream_t)stream);
+    sampler_plan_free(S);
     return rc;
 }

@@ -85,6 +85,12 @@ _SIGNATURES = {
     "pq_permanent_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp]),
     "pq_bs_sample": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "pq_bs_probs_lossy": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp]),
+    "pq_lossy_plan_create": (_i32, [_i32, _vp, _vp, _i64, ctypes.POINTER(_vp)]),
+    "pq_lossy_plan_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "pq_lossy_plan_destroy": (_i32, [_vp]),
+    "pq_sampler_plan_create": (_i32, [_i32, _vp, _i64, ctypes.POINTER(_vp)]),
+    "pq_sampler_plan_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "pq_sampler_plan_destroy": (_i32, [_vp]),
     "pq_hafnian_repeated": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "pq_loop_hafnian_repeated": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "pq_hafnian_plan_create": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, ctypes.POINTER(_vp)]),
@@ -392,6 +398,53 @@ def pq_debug_live_allocations() -> tuple[int, int]:
 
 def pq_debug_corrupt_plan(plan: int, what: int) -> None:
     _check(load_library().pq_debug_corrupt_plan(plan, what), "pq_debug_corrupt_plan")
+
+
+def pq_lossy_plan_create(m: int, input_occ, output_occ) -> int:
+    """Plan lossy probabilities for host occupations; returns the handle."""
+    s = np.ascontiguousarray(input_occ, dtype=np.int32)
+    t = np.ascontiguousarray(output_occ, dtype=np.int32).reshape(-1, m)
+    h = _vp()
+    _check(load_library().pq_lossy_plan_create(m, s.ctypes.data, t.ctypes.data if t.size else None,
+                                               t.shape[0], ctypes.byref(h)),
+           "pq_lossy_plan_create")
+    return h.value
+
+
+def pq_lossy_plan_run(plan: int, V_ptr, eta_ptr, W_ptr, probs_ptr, stream):
+    _check(load_library().pq_lossy_plan_run(plan, V_ptr, eta_ptr, W_ptr, probs_ptr, stream),
+           "pq_lossy_plan_run")
+
+
+def pq_lossy_plan_destroy(plan: int):
+    _check(load_library().pq_lossy_plan_destroy(plan), "pq_lossy_plan_destroy")
+
+
+def pq_sampler_plan_create(m: int, input_occ, nsamples: int) -> int:
+    """Plan nsamples Algorithm A draws per run for a host input occupation."""
+    s = np.ascontiguousarray(input_occ, dtype=np.int32)
+    h = _vp()
+    _check(load_library().pq_sampler_plan_create(m, s.ctypes.data, nsamples, ctypes.byref(h)),
+           "pq_sampler_plan_create")
+    return h.value
+
+
+def pq_sampler_plan_run(plan: int, U_ptr, m: int, col_order: np.ndarray, uniforms: np.ndarray,
+                        stream) -> np.ndarray:
+    """One planned run; col_order and uniforms are host arrays (nsamples x n).
+    Returns nsamples x m occupations."""
+    co = np.ascontiguousarray(col_order, dtype=np.int32)
+    un = np.ascontiguousarray(uniforms, dtype=np.float64)
+    out = np.zeros((co.shape[0], m), dtype=np.int32)
+    _check(load_library().pq_sampler_plan_run(plan, U_ptr, co.ctypes.data if co.size else None,
+                                              un.ctypes.data if un.size else None,
+                                              out.ctypes.data if out.size else None, stream),
+           "pq_sampler_plan_run")
+    return out
+
+
+def pq_sampler_plan_destroy(plan: int):
+    _check(load_library().pq_sampler_plan_destroy(plan), "pq_sampler_plan_destroy")
 
 
 def pq_version() -> str:

@@ -54,3 +54,30 @@ def test_lossy_rejects_too_many_photons(dev):
     with pytest.raises(pq.PQError) as e:
         api.bs_probs_lossy(I, eta, I, [1, 0, 0], [[1, 1, 0]])
     assert e.value.code == pq.PQ_ERR_ARG
+
+
+def test_lossy_plan_runs_match_the_one_shot_call(dev):
+    """A lossy plan made once evaluates, run after run, what the one-shot call
+    gives for each new interferometer (same schedule, same bits), and the
+    oracle's probabilities."""
+    m = 5
+    s = np.array([1, 1, 0, 1, 0], dtype=np.int32)
+    t = patterns_upto(3, m)
+    plan = api.LossyPlan(m, s, t)
+    rng = np.random.default_rng(91)
+    for _ in range(3):
+        V, Wm = W.haar_unitary(m, rng), W.haar_unitary(m, rng)
+        eta = rng.uniform(0.2, 0.95, m)
+        Vd, Wd, ed = (torch.from_numpy(x).to(dev) for x in (V, Wm, eta))
+        got = plan.run(Vd, ed, Wd).cpu().numpy()
+        want = api.bs_probs_lossy(Vd, ed, Wd, s, t).cpu().numpy()
+        assert np.array_equal(got, want)
+        ref = O.lossy_probs(V, eta, Wm, s, t)
+        assert (np.abs(got - ref) <= 1e-10 * ref + 1e-16).all()
+    plan.close()
+    empty = api.LossyPlan(m, s, np.zeros((0, m), dtype=np.int32))
+    I = torch.eye(m, dtype=torch.complex128, device=dev)
+    assert empty.run(I, torch.ones(m, dtype=torch.float64, device=dev), I).numel() == 0
+    with pytest.raises(pq.PQError) as e:
+        api.LossyPlan(m, s, [[1, 1, 1, 1, 0]])  # more photons than the input
+    assert e.value.code == pq.PQ_ERR_ARG

@@ -150,3 +150,31 @@ def test_sampler_argument_errors(dev):
     with pytest.raises(pq.PQError) as e:  # uniform outside [0, 1)
         api.bs_sample(U, s, np.array([[0, 1]], dtype=np.int32), np.array([[0.1, 1.0]]))
     assert e.value.code == pq.PQ_ERR_ARG
+
+
+def test_sampler_plan_runs_match_the_one_shot_call(dev):
+    """A planned sampler run gives, sample for sample, what pq_bs_sample gives
+    for the same interferometer, column orders and uniforms: on three runs in
+    a row with different interferometers and draws (the workspace is reused),
+    and with the step plans made once."""
+    s = np.array([1, 0, 1, 1, 0, 1, 0, 0], dtype=np.int32)
+    m, ns, n = 8, 300, 4
+    plan = api.SamplerPlan(m, s, ns)
+    try:
+        for run in range(3):
+            U = torch.from_numpy(W.haar_unitary(m, np.random.default_rng(50 + run))).to(dev)
+            order, unif = W.sampler_draws(ns, n, 60 + run)
+            got = plan.run(U, order, unif)
+            want = api.bs_sample(U, s, order, unif)
+            assert np.array_equal(got, want), run
+            assert (got.sum(axis=1) == n).all()
+        with pytest.raises(ValueError):
+            plan.run(U, order[:10], unif[:10])
+        with pytest.raises(pq.PQError) as e:  # not a permutation: checked before any launch
+            bad = order.copy()
+            bad[3, 1] = bad[3, 0]
+            plan.run(U, bad, unif)
+        assert e.value.code == pq.PQ_ERR_ARG
+        assert np.array_equal(plan.run(U, order, unif), want)  # usable after the error
+    finally:
+        plan.close()
