@@ -248,7 +248,8 @@ __device__ __forceinline__ void bwd_term(const double2* S, double2* P, double2* 
     A[0] = av;
 }
 
-__device__ void bwd_stage(const BwdArgs& a, const PermDesc& D, const MetaView& mv, BwdSmem& sm,
+template <class SM>
+__device__ void bwd_stage(const BwdArgs& a, const PermDesc& D, const MetaView& mv, SM& sm,
                           int lane)
 {
     const int k = D.k, l = D.l;
@@ -281,6 +282,8 @@ __device__ void bwd_stage(const BwdArgs& a, const PermDesc& D, const MetaView& m
     }
     __syncwarp();
 }
+
+__device__ void bwd_combine(const BwdArgs& a, const Task& t, const PermDesc& D, int kl, int lane);
 
 __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& staged, int lane)
 {
@@ -451,7 +454,13 @@ __device__ void bwd_task(const BwdArgs& a, const Task& t, BwdSmem& sm, int& stag
         }
     }
 
-    // ---- combine the tasks of this permanent
+    bwd_combine(a, t, D, kl, lane);
+}
+
+// The tasks of a permanent are summed in task order by the warp that finishes
+// last, and the sum is scaled by 2^{1-n} and the upstream gradient.
+__device__ void bwd_combine(const BwdArgs& a, const Task& t, const PermDesc& D, int kl, int lane)
+{
     int last = 1;
     if (D.ntasks > 1) {
         __threadfence();  // every lane's slot entries, before the count
@@ -551,6 +560,335 @@ __global__ void __launch_bounds__(256, 2) glynn_bwd_kernel(BwdArgs a, int64_t t_
             continue;
         }
         bwd_task(a, a.tasks[ti], sm, staged, lane);
+    }
+}
+
+// ---------------------------------------------------------------- register-resident walk
+// For product-column bounds NL <= 14 a lane keeps its column sums S, its
+// accumulators A and the term's prefixes P in registers: every column loop is
+// unrolled over NL and columns j >= l are skipped by warp-uniform tests.  Only
+// the correction rows C stay in shared memory, so a warp needs about a third
+// of the shared memory of the kernel above and more warps fit on an SM (the
+// FP64 pipe of an SM sub-partition with a single warp idles whenever that
+// warp waits on a dependent result).
+//
+// The factor c_j of the repeated columns is applied once, when the task's
+// gradient is written: the lanes accumulate A'_j = sum_t w_t Q_j(t) / c_j,
+// and everything built from A' (the corrections, the contraction) is linear
+// in it.  A column with c_j >= 2 then costs, per term, (c_j - 1) extra
+// complex products in the prefix pass and (c_j - 1) in the suffix pass:
+// t = sw S_j^{c_j - 1}, A'_j += P_j t, sw = t S_j.
+//
+// Per-warp shared memory: base matrix M (kmax x ld), base column sums (ld),
+// a region that holds the correction rows C (jb x ld x kLS) during the walk
+// and, at the end of a task, the accumulators A' (ld x kLS) and the row
+// multipliers X (kmax x kLS doubles), then the correction sums V (jb x ld),
+// the weights wh (32) and small integer arrays.
+__host__ __device__ inline long bwdr_region_bytes(int kmax, int ld, int jb)
+{
+    const long walk = 16L * kLS * jb * ld;
+    const long end = 16L * kLS * ld + ((8L * kLS * kmax + 15) & ~15L);
+    return walk > end ? walk : end;
+}
+
+__host__ __device__ inline int bwdr_warp_smem_bytes(int kmax, int ld, int jb)
+{
+    const long bytes = 16L * (kmax * ld + ld) + bwdr_region_bytes(kmax, ld, jb) + 16L * jb * ld +
+                       8L * 32 + 4L * (16 + ld + kmax);
+    return (int)((bytes + 15) & ~15L);
+}
+
+struct BwdRegSmem {
+    double2* M;       // kmax x ld
+    double2* base;    // ld
+    double2* C;       // jb x ld x kLS    -- region, during the walk
+    double2* A;       // ld x kLS         -- region, at the end of a task
+    double* X;        // kmax x kLS       -- region, at the end of a task
+    double2* V;       // jb x ld
+    double* wh;       // 32
+    int32_t* lowrow;  // 16
+    int32_t* cm;      // ld
+    int32_t* rowdig;  // kmax
+    int ld;
+    __device__ BwdRegSmem(unsigned char* raw, int kmax, int ld_, int jb)
+    {
+        ld = ld_;
+        M = reinterpret_cast<double2*>(raw);
+        base = M + kmax * ld;
+        C = base + ld;
+        A = C;
+        X = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(C) + 16L * kLS * ld);
+        V = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(C) +
+                                       bwdr_region_bytes(kmax, ld, jb));
+        wh = reinterpret_cast<double*>(V + jb * ld);
+        lowrow = reinterpret_cast<int32_t*>(wh + 32);
+        cm = lowrow + 16;
+        rowdig = cm + ld;
+    }
+};
+
+// One term: A'_j += ws Q_j / c_j for j < l.  n2 = number of leading columns
+// with c_j >= 2 (their multiplicities in cm).
+template <int NL>
+__device__ __forceinline__ void bwdr_term(const double2 (&S)[NL], double2 (&A)[NL],
+                                          const int (&cm)[NL], int l, int n2, double ws)
+{
+    // prefixes P_j = prod_{j' < j} S_{j'}^{c_{j'}}, j = 1 .. l-1
+    double2 P[NL];
+    double2 run = S[0];
+    if (n2 > 0) {
+#pragma unroll 1
+        for (int e = 1; e < cm[0]; ++e)
+            run = cmul(run, S[0]);
+    }
+    P[NL > 1 ? 1 : 0] = run;
+#pragma unroll
+    for (int j = 1; j < NL - 1; ++j) {
+        if (j < l - 1) {
+            run = cmul(run, S[j]);
+            if (j < n2) {
+#pragma unroll 1
+                for (int e = 1; e < cm[j]; ++e)
+                    run = cmul(run, S[j]);
+            }
+            P[j + 1] = run;
+        }
+    }
+    // suffix pass, last column first; sw = ws prod_{j' > j} S_{j'}^{c_{j'}}
+    // (a separate branch for the last column, whose suffix is real, made the
+    // compiler keep S, A and P in local memory)
+    double2 sw = make_double2(ws, 0.0);
+#pragma unroll
+    for (int j = NL - 1; j >= 1; --j) {
+        if (j < l) {
+            double2 t = sw;
+            if (j < n2) {
+#pragma unroll 1
+                for (int e = 1; e < cm[j]; ++e)
+                    t = cmul(t, S[j]);
+            }
+            cfma_acc<false>(A[j], P[j], t);
+            sw = cmul(t, S[j]);
+        }
+    }
+    // column 0: S_0^{c_0 - 1} times the suffix (for l = 1 the weight alone)
+    double2 t = sw;
+    if (n2 > 0) {
+#pragma unroll 1
+        for (int e = 1; e < cm[0]; ++e)
+            t = cmul(t, S[0]);
+    }
+    A[0].x = __dadd_rn(A[0].x, t.x);
+    A[0].y = __dadd_rn(A[0].y, t.y);
+}
+
+template <int NL>
+__device__ void bwdr_task(const BwdArgs& a, const Task& t, BwdRegSmem& sm, int& staged, int lane)
+{
+    const PermDesc D = a.desc[t.perm];
+    const MetaView mv = meta_view(a.meta, D);
+    const int k = D.k, l = D.l, J = D.J, ndig = D.ndig;
+    const int kl = k * l;
+    double* slot = a.gpart + 2 * (a.gpart_off[t.perm] + (int64_t)t.part * kl);
+
+    if (!D.trivial) {
+        __syncwarp();  // the previous task's contraction read the region that C reuses
+        if (staged != t.perm) {
+            bwd_stage(a, D, mv, sm, lane);
+            staged = t.perm;
+        }
+        const int64_t chunk0 = (int64_t)t.part * kWarp;
+        const bool active = chunk0 + lane < D.nchunks;
+        const int64_t chunk = active ? (chunk0 + lane) : 0;
+        double2 S[NL], A[NL];
+        int cm[NL];
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+            S[j] = j < l ? sm.base[j] : make_double2(0.0, 0.0);
+            A[j] = make_double2(0.0, 0.0);
+            cm[j] = j < l ? sm.cm[j] : 1;
+        }
+        // the high digits of this lane's chunk: column sums and weight
+        uint64_t whigh_u = 1;
+        int gpar = 0;
+        int64_t c = chunk;
+#pragma unroll 1
+        for (int d = J; d < ndig; ++d) {
+            const int rad = mv.drad[d];
+            const int g = (int)(c % rad);
+            c /= rad;
+            if (g == 0)
+                continue;
+            const double2* Mr = sm.M + mv.drow[d] * NL;
+            const double coef = (double)(-2 * g);
+#pragma unroll
+            for (int j = 0; j < NL; ++j) {
+                if (j < l) {
+                    const double2 b = Mr[j];
+                    S[j].x = __fma_rn(coef, b.x, S[j].x);
+                    S[j].y = __fma_rn(coef, b.y, S[j].y);
+                }
+            }
+            whigh_u *= binom_u64(mv.dtop[d], g);
+            gpar += g;
+        }
+        double whigh = active ? (double)whigh_u : 0.0;
+        if (gpar & 1)
+            whigh = -whigh;
+        sm.wh[lane] = whigh;
+        for (int e = 0; e < J * l; ++e) {
+            const int d = e / l, j = e - d * l;
+            sm.C[(d * NL + j) * kLS + lane] = make_double2(0.0, 0.0);
+        }
+        int n2 = 0;
+        while (n2 < l && sm.cm[n2] >= 2)
+            ++n2;
+        uint32_t lowrows = 0;  // row of low digit d in bits [6d, 6d + 6): rows < 64
+        for (int d = 0; d < J; ++d)
+            lowrows |= (uint32_t)sm.lowrow[d] << (6 * d);
+
+        LowWalk wk;
+        wk.v = 0;
+        wk.g = 0;
+        wk.dir = 0;
+        wk.radm1 = 0;
+        wk.topp = 0;
+        for (int d = 0; d < J; ++d) {
+            wk.radm1 |= uint64_t(mv.drad[d] - 1) << (4 * d);
+            wk.topp |= uint64_t(mv.dtop[d]) << (4 * d);
+        }
+        double wlow = 1.0;
+        const int64_t L = D.L;
+#pragma unroll 1
+        for (int64_t s = 0; s < L; ++s) {
+            bwdr_term<NL>(S, A, cm, l, n2, (s & 1) ? -wlow : wlow);
+            if (s + 1 < L) {
+                int up;
+                const int d = low_step(wk, up);
+                const int row = (int)((lowrows >> (6 * d)) & 63u);
+                const double delta = up > 0 ? -2.0 : 2.0;
+                const double2* Mr = sm.M + row * NL;
+                double2* Cd = sm.C + d * NL * kLS + lane;
+#pragma unroll
+                for (int j = 0; j < NL; ++j) {
+                    if (j < l) {
+                        const double2 b = Mr[j];
+                        double2 cv = Cd[j * kLS];
+                        S[j].x = __fma_rn(delta, b.x, S[j].x);
+                        S[j].y = __fma_rn(delta, b.y, S[j].y);
+                        cv.x = __fma_rn(delta, A[j].x, cv.x);
+                        cv.y = __fma_rn(delta, A[j].y, cv.y);
+                        Cd[j * kLS] = cv;
+                    }
+                }
+                if (((wk.radm1 >> (4 * d)) & 15u) > 1u)
+                    wlow = (double)low_weight(wk, J);
+            }
+        }
+        // Contraction, as in the kernel above: V from the corrections first,
+        // then the accumulators and row multipliers go to the region that
+        // held the corrections.
+        __syncwarp();
+        for (int e = lane; e < J * l; e += kWarp) {
+            const int d = e / l, j = e - d * l;
+            const double2* Cq = sm.C + (d * NL + j) * kLS;
+            double vx = 0.0, vy = 0.0;
+            for (int q = 0; q < 32; ++q) {
+                const double2 cv = Cq[q];
+                vx = __fma_rn(sm.wh[q], cv.x, vx);
+                vy = __fma_rn(sm.wh[q], cv.y, vy);
+            }
+            sm.V[d * NL + j] = make_double2(vx, vy);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < NL; ++j)
+            if (j < l)
+                sm.A[j * kLS + lane] = A[j];
+        {
+            const double whl = sm.wh[lane];
+            double* X = sm.X + lane;
+            for (int i = 0; i < k; ++i)
+                X[i * kLS] = whl * (double)mv.rmul[i];
+            int64_t cc = chunk;
+            for (int d = J; d < ndig; ++d) {
+                const int rad = mv.drad[d];
+                const int g = (int)(cc % rad);
+                cc /= rad;
+                const int row = mv.drow[d];
+                X[row * kLS] = whl * (double)(mv.rmul[row] - 2 * g);
+            }
+            for (int d = 0; d < J; ++d) {
+                const int g = (int)((wk.g >> (4 * d)) & 15u);
+                const int row = sm.lowrow[d];
+                X[row * kLS] = whl * (double)(mv.rmul[row] - 2 * g);
+            }
+        }
+        __syncwarp();
+        for (int e = lane; e < kl; e += kWarp) {
+            const int i = e / l, j = e - i * l;
+            const int dg = sm.rowdig[i];
+            const double2* Aq = sm.A + j * kLS;
+            const double* uq = sm.X + i * kLS;
+            double gx = 0.0, gy = 0.0;
+            for (int q = 0; q < 32; ++q) {
+                const double2 av = Aq[q];
+                gx = __fma_rn(uq[q], av.x, gx);
+                gy = __fma_rn(uq[q], av.y, gy);
+            }
+            if (dg >= 0) {
+                const double2 v = sm.V[dg * NL + j];
+                gx = __dsub_rn(gx, v.x);
+                gy = __dsub_rn(gy, v.y);
+            }
+            const double cj = (double)sm.cm[j];
+            slot[2 * e] = cj * gx;
+            slot[2 * e + 1] = cj * gy;
+        }
+    }
+    bwd_combine(a, t, D, kl, lane);
+}
+
+// The register-resident kernel for product-column bound NL (the launch's
+// class bound); the guards are those of the kernel above, without a bound on
+// the repeated columns.
+template <int NL>
+__global__ void __launch_bounds__(256) glynn_bwd_reg_kernel(BwdArgs a, int64_t t_begin,
+                                                            int64_t t_end, int kmax, int jb,
+                                                            int queue)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    BwdRegSmem sm(smem_raw + warp * bwdr_warp_smem_bytes(kmax, NL, jb), kmax, NL, jb);
+    int staged = -1;
+    if (!queue) {
+        const int64_t ti = t_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+        if (ti >= t_end)
+            return;
+        const int32_t bad = bwd_guard(a, ti, kmax, NL, jb, NL);
+        if (bad) {
+            if (lane == 0)
+                record_error(a.err, bad, ti);
+            return;
+        }
+        bwdr_task<NL>(a, a.tasks[ti], sm, staged, lane);
+        return;
+    }
+    for (;;) {
+        int q = 0;
+        if (lane == 0)
+            q = atomicAdd(a.counters, 1);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        const int64_t ti = t_begin + q;
+        if (ti >= t_end)
+            break;
+        const int32_t bad = bwd_guard(a, ti, kmax, NL, jb, NL);
+        if (bad) {
+            if (lane == 0)
+                record_error(a.err, bad, ti);
+            continue;
+        }
+        bwdr_task<NL>(a, a.tasks[ti], sm, staged, lane);
     }
 }
 
@@ -677,6 +1015,85 @@ cudaError_t bwd_launch_plain(int ld, const BwdArgs& a, int64_t t_begin, int64_t 
     const unsigned grid = (unsigned)((nt + wpb - 1) / wpb);
     glynn_bwd_kernel<<<grid, 32 * wpb, smem, st>>>(a, t_begin, t_end, kmax, ld, jb, n2, 0);
     return cudaGetLastError();
+}
+
+// ---- register-resident walk
+bool bwdr_supported(int ld) { return ld >= 2 && ld <= kBwdRegMaxLd && ld % 2 == 0; }
+
+int bwdr_smem_bytes_for(int kmax, int ld, int jb) { return bwdr_warp_smem_bytes(kmax, ld, jb); }
+
+static const void* bwdr_kernel_for(int ld)
+{
+    switch (ld) {
+    case 2: return (const void*)glynn_bwd_reg_kernel<2>;
+    case 4: return (const void*)glynn_bwd_reg_kernel<4>;
+    case 6: return (const void*)glynn_bwd_reg_kernel<6>;
+    case 8: return (const void*)glynn_bwd_reg_kernel<8>;
+    case 10: return (const void*)glynn_bwd_reg_kernel<10>;
+    case 12: return (const void*)glynn_bwd_reg_kernel<12>;
+    case 14: return (const void*)glynn_bwd_reg_kernel<14>;
+    default: return nullptr;
+    }
+}
+
+int bwdr_regs_per_thread(int ld)
+{
+    cudaFuncAttributes at{};
+    const void* f = bwdr_kernel_for(ld);
+    return (f && cudaFuncGetAttributes(&at, f) == cudaSuccess) ? at.numRegs : 255;
+}
+
+// Raise (never lower) the dynamic shared-memory limit of the class's kernel.
+cudaError_t bwdr_prepare(int ld, int smem_bytes)
+{
+    const void* f = bwdr_kernel_for(ld);
+    if (!f)
+        return cudaErrorInvalidValue;
+    cudaFuncAttributes at{};
+    cudaError_t e = cudaFuncGetAttributes(&at, f);
+    if (e != cudaSuccess)
+        return e;
+    if (at.maxDynamicSharedSizeBytes >= smem_bytes)
+        return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+template <int NL>
+static void bwdr_launch_nl(const BwdArgs& a, int64_t t_begin, int64_t t_end, int kmax, int jb,
+                           unsigned grid, int wpb, int queue, cudaStream_t st)
+{
+    glynn_bwd_reg_kernel<NL><<<grid, 32 * wpb, wpb * bwdr_warp_smem_bytes(kmax, NL, jb), st>>>(
+        a, t_begin, t_end, kmax, jb, queue);
+}
+
+static cudaError_t bwdr_launch(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end, int kmax,
+                               int jb, unsigned grid, int wpb, int queue, cudaStream_t st)
+{
+    switch (ld) {
+    case 2: bwdr_launch_nl<2>(a, t_begin, t_end, kmax, jb, grid, wpb, queue, st); break;
+    case 4: bwdr_launch_nl<4>(a, t_begin, t_end, kmax, jb, grid, wpb, queue, st); break;
+    case 6: bwdr_launch_nl<6>(a, t_begin, t_end, kmax, jb, grid, wpb, queue, st); break;
+    case 8: bwdr_launch_nl<8>(a, t_begin, t_end, kmax, jb, grid, wpb, queue, st); break;
+    case 10: bwdr_launch_nl<10>(a, t_begin, t_end, kmax, jb, grid, wpb, queue, st); break;
+    case 12: bwdr_launch_nl<12>(a, t_begin, t_end, kmax, jb, grid, wpb, queue, st); break;
+    case 14: bwdr_launch_nl<14>(a, t_begin, t_end, kmax, jb, grid, wpb, queue, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t bwdr_launch_persistent(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end,
+                                   int kmax, int jb, int blocks, int wpb, cudaStream_t st)
+{
+    return bwdr_launch(ld, a, t_begin, t_end, kmax, jb, (unsigned)blocks, wpb, 1, st);
+}
+
+cudaError_t bwdr_launch_plain(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end, int kmax,
+                              int jb, int wpb, cudaStream_t st)
+{
+    const int64_t nt = t_end - t_begin;
+    return bwdr_launch(ld, a, t_begin, t_end, kmax, jb, (unsigned)((nt + wpb - 1) / wpb), wpb, 0,
+                       st);
 }
 
 cudaError_t scatter_grad_batch(const PermDesc* desc, const int32_t* meta, int64_t nperm,

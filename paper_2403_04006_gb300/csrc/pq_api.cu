@@ -313,11 +313,24 @@ static double bwd_flops_per_term(const ItemPlan& it)
 // accumulation of prefix times weighted suffix and the suffix update, 8; the
 // end columns and the weighted suffix's start 6; per repeated column its
 // powers, the scaled derivative and one more product, 4(c - 1) + 6.
-static double bwd_instr_per_term(const ItemPlan& it)
+static double bwd_instr_per_term(const ItemPlan& it, bool reg)
 {
     if (it.n == 1)
         return 2.0;
     const int l = it.l;
+    if (reg) {
+        // register-resident walk: the step 4l, column 0's add 2; prefix
+        // products c_j for columns 1 .. l-2 and c_0 - 1 for column 0; per
+        // suffix column j >= 1 its c_j - 1 powers, the accumulation and the
+        // suffix update, 4(c_j - 1) + 8; column 0's c_0 - 1 powers
+        const std::vector<int32_t>& c = it.cmul;
+        double v = 4.0 * l + 2.0 + 8.0 * (c[0] - 1);
+        for (int j = 1; j < l - 1; ++j)
+            v += 4.0 * c[j];
+        for (int j = 1; j < l; ++j)
+            v += 4.0 * (c[j] - 1) + 8.0;
+        return v;
+    }
     double rep = 0.0;
     for (int c : it.cmul)
         if (c >= 2)
@@ -1176,14 +1189,17 @@ static int ensure_backward(pq_plan* P)
         if (!cls_used[c])
             continue;
         BwdClass& C = cls[c];
+        C.reg = bwdr_supported(C.ld) ? 1 : 0;
+        const int regs = C.reg ? bwdr_regs_per_thread(C.ld) : bwd_regs_per_thread(C.ld);
         const double nbar = cls_terms[c] > 0 ? cls_nterms[c] / cls_terms[c] : 1.0;
         double best = -1.0;
         for (int J = kBwdMaxLowDigits; J >= 1; --J) {
-            const int per_warp = bwd_smem_bytes_for(C.kmax, C.ld, J, C.n2);
+            const int per_warp = C.reg ? bwdr_smem_bytes_for(C.kmax, C.ld, J)
+                                       : bwd_smem_bytes_for(C.kmax, C.ld, J, C.n2);
             if (per_warp > 200 * 1024)
                 continue;
             int wpb = 0, bps = 0;
-            launch_geometry_max(bwd_regs_per_thread(C.ld), per_warp, 8, wpb, bps);
+            launch_geometry_max(regs, per_warp, 8, wpb, bps);
             const double warps = std::min(8.0, (double)(wpb * bps)) / 8.0;
             const double per_term = 16.0 * C.ld - 10.0;
             const double start = std::max(0.0, nbar - J) * 2.0 * C.ld / (double)(1 << J);
@@ -1232,7 +1248,7 @@ static int ensure_backward(pq_plan* P)
         if (!it.trivial) {
             // every lane of a task walks L terms and starts its chunk from the
             // high digits; the task ends with the lane contraction
-            const double lane = (double)it.L * bwd_instr_per_term(it) +
+            const double lane = (double)it.L * bwd_instr_per_term(it, C.reg != 0) +
                                 2.0 * it.l * (double)((int)it.drad.size() - it.J);
             instr_b += (double)nt * (32.0 * lane + 32.0 * it.k + 64.0 * it.J * it.l + 66.0 * kl);
         }
@@ -1317,7 +1333,14 @@ static int ensure_backward(pq_plan* P)
     }
     int max_smem = 0, jb = 0, n2 = 0;
     for (const BwdClass& C : P->bwd_classes) {
-        max_smem = std::max(max_smem, C.wpb * bwd_smem_bytes_for(C.kmax, C.ld, C.jb, C.n2));
+        if (C.reg) {
+            cudaError_t e = bwdr_prepare(C.ld, C.wpb * bwdr_smem_bytes_for(C.kmax, C.ld, C.jb));
+            if (e != cudaSuccess)
+                return fail(PQ_ERR_CUDA, "backward attribute setup failed: %s",
+                            cudaGetErrorString(e));
+        } else {
+            max_smem = std::max(max_smem, C.wpb * bwd_smem_bytes_for(C.kmax, C.ld, C.jb, C.n2));
+        }
         jb = std::max(jb, C.jb);
         n2 = std::max(n2, C.n2);
     }
@@ -1368,8 +1391,10 @@ static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, co
         a.tasks = P->tasks_bwd_plain_d;
         for (int64_t p = 0; p < P->nperm; ++p) {
             const BwdClass& C = P->bwd_classes[P->bwd_class_of[p]];
-            e = bwd_launch_plain(C.ld, a, P->plain_first_bwd[p], P->plain_first_bwd[p + 1],
-                                 C.kmax, C.jb, C.n2, C.wpb, st);
+            e = C.reg ? bwdr_launch_plain(C.ld, a, P->plain_first_bwd[p],
+                                          P->plain_first_bwd[p + 1], C.kmax, C.jb, C.wpb, st)
+                      : bwd_launch_plain(C.ld, a, P->plain_first_bwd[p], P->plain_first_bwd[p + 1],
+                                         C.kmax, C.jb, C.n2, C.wpb, st);
             if (e != cudaSuccess)
                 return fail(PQ_ERR_CUDA, "plain backward launch failed: %s", cudaGetErrorString(e));
         }
@@ -1381,8 +1406,10 @@ static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, co
             const BwdClass& C = P->bwd_classes[c];
             if (c > 0)
                 PQ_CUDA(cudaMemsetAsync(P->counters_d, 0, sizeof(int32_t), st));
-            e = bwd_launch_persistent(C.ld, a, C.t_begin, C.t_end, C.kmax, C.jb, C.n2, C.blocks,
-                                      C.wpb, st);
+            e = C.reg ? bwdr_launch_persistent(C.ld, a, C.t_begin, C.t_end, C.kmax, C.jb,
+                                               C.blocks, C.wpb, st)
+                      : bwd_launch_persistent(C.ld, a, C.t_begin, C.t_end, C.kmax, C.jb, C.n2,
+                                              C.blocks, C.wpb, st);
             if (e != cudaSuccess)
                 return fail(PQ_ERR_CUDA, "backward launch failed: %s", cudaGetErrorString(e));
         }

@@ -91,6 +91,17 @@ cudaError_t bwd_launch_persistent(int ld, const BwdArgs& a, int64_t t_begin, int
                                   int kmax, int jb, int n2, int blocks, int wpb, cudaStream_t st);
 cudaError_t bwd_launch_plain(int lmax, const BwdArgs& a, int64_t t_begin, int64_t t_end,
                              int kmax, int jb, int n2, int wpb, cudaStream_t st);
+// The register-resident walk (column sums, accumulators and prefixes in
+// registers) for even product-column bounds up to kBwdRegMaxLd.
+constexpr int kBwdRegMaxLd = 14;
+bool bwdr_supported(int ld);
+int bwdr_smem_bytes_for(int kmax, int ld, int jb);
+int bwdr_regs_per_thread(int ld);
+cudaError_t bwdr_prepare(int ld, int smem_bytes);
+cudaError_t bwdr_launch_persistent(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end,
+                                   int kmax, int jb, int blocks, int wpb, cudaStream_t st);
+cudaError_t bwdr_launch_plain(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end, int kmax,
+                              int jb, int wpb, cudaStream_t st);
 
 // Scatter of oriented per-permanent gradients into the caller's layouts.
 cudaError_t scatter_grad_batch(const PermDesc* desc, const int32_t* meta, int64_t nperm,

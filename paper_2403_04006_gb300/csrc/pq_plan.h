@@ -31,6 +31,7 @@ struct ItemPlan {
 // with the shared-memory layout sized for them.
 struct BwdClass {
     int ld = 1, kmax = 1, jb = 0, n2 = 0, wpb = 1, blocks = 1;
+    int reg = 0;  // 1: the register-resident walk (glynn_bwd_reg_kernel)
     int64_t t_begin = 0, t_end = 0;  // range in the batched backward task list
 };
 
