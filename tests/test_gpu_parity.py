@@ -407,6 +407,51 @@ def test_permanent_backward_large_product_sides(dev):
             assert np.abs(got - refs[b]).max() <= TOLG * np.abs(refs[b]).max()
 
 
+def width_items(rng):
+    """For every product width l = 1 .. 16 one item with distinct product
+    columns and one with repeated ones (up to 4 copies for l <= 8, 2 above),
+    the summed side repeated more (parts of 2 to 4), so that the planner keeps
+    the repeated columns on the product side."""
+    items = []
+    for l in range(1, 17):
+        for cmax in ((1, 4) if l <= 8 else (1, 2)):
+            c = sorted((int(x) for x in rng.integers(1, cmax + 1, size=l)), reverse=True)
+            if cmax > 1:
+                c[0] = cmax
+            n = sum(c)
+            r, left = [], n
+            while left:
+                p = min(int(rng.integers(2, 5)), left)
+                r.append(p)
+                left -= p
+            B = (rng.standard_normal((len(r), l)) + 1j * rng.standard_normal((len(r), l)))
+            items.append((B / math.sqrt(2 * n), r, c))
+    return items
+
+
+def test_backward_every_product_width(dev):
+    """Every backward launch class: product widths 1 .. 14 (the
+    register-resident walk, odd and even widths of each class bound) and 15,
+    16 (the shared-memory kernel), with and without repeated product columns,
+    both methods, against the oracle's Laplace minors."""
+    items = width_items(np.random.default_rng(408))
+    pb = W.pack_batch(items)
+    widths = product_columns(pb)
+    assert set(range(1, 17)) <= set(int(w) for w in widths)
+    db = api.DeviceBatch(pb, dev)
+    rng = np.random.default_rng(409)
+    gout = (rng.standard_normal(pb.batch) + 1j * rng.standard_normal(pb.batch))
+    refs = [gout[b] * np.conj(O.perm_grad(B, r, c, gold=True)) for b, (B, r, c) in enumerate(items)]
+    for method in ("batched", "plain"):
+        plan = api.Plan.for_batch(pb, method=method)
+        g = api.permanent_backward(db, torch.from_numpy(gout).to(dev), plan).cpu().numpy()
+        for b, (B, r, c) in enumerate(items):
+            o = int(pb.mat_off[b])
+            got = g[o:o + B.size].reshape(B.shape)
+            assert np.abs(got - refs[b]).max() <= TOLG * np.abs(refs[b]).max(), (method, b)
+        assert pq.pq_plan_device_error(plan.handle) == (0, 0)
+
+
 def test_permanent_gradcheck(dev):
     rng = np.random.default_rng(505)
     items = random_items(4, 2, 5, rng)
