@@ -216,12 +216,18 @@ def load_workload(name: str, block: int = 0):
     raise ValueError(f"unknown workload {name}")
 
 
-def bench_config(desc: str, permanents: int, terms: int, world: int) -> dict:
+def bench_config(desc: str, permanents: int, terms: int, world: int, split: bool = False) -> dict:
     """The workload the line measures; both arms print this same object."""
+    if world == 1:
+        par = "1 GPU"
+    elif split:
+        par = (f"{world} ranks, one batch of {permanents} permanents split by whole permanents "
+               "with balanced work (pq_partition_batch), outputs all-gathered in every timed step")
+    else:
+        par = (f"{world} ranks, block r of a batch of {world} x {permanents // world} "
+               "permanents on rank r, no collective on the data path")
     return {"workload": desc, "permanents": permanents, "terms": terms,
-            "parallelism": (f"{world} ranks, block r of a batch of {world} x {permanents} "
-                            "permanents on rank r, no collective on the data path"
-                            if world > 1 else "1 GPU"),
+            "parallelism": par,
             "l2": "GPU arm: flushed (256 MB write) before every timed step; "
                   "CPU arm: inputs in host memory"}
 
@@ -320,7 +326,14 @@ def bench_ours(args):
 
     if args.workload in PROFILE_CASES:
         return bench_case(args, dev)
-    pb, workload_desc = load_workload(args.workload, block=rank)
+    split = args.split and world > 1
+    if split:
+        # strong scaling: one batch, each rank its share of whole permanents
+        full, workload_desc = load_workload(args.workload, block=0)
+        rank_of, _ = api.partition_batch(full, world)
+        pb = full.subset(np.nonzero(rank_of == rank)[0])
+    else:
+        pb, workload_desc = load_workload(args.workload, block=rank)
     db = api.DeviceBatch(pb, dev)
     plan = api.Plan.for_batch(pb, method="batched", use_graph=True, chunk_log2=args.chunk_log2)
     if not args.no_autotune and args.chunk_log2 == 0:
@@ -332,6 +345,8 @@ def bench_ours(args):
 
     def step():
         api.permanent_batched(db, plan, out=out, stream=stream)
+        if split:  # every rank ends the step with the whole batch's outputs
+            api.gather_partitioned(out, rank_of)
 
     # FP64 peak: 2 lane-operations per clock per SM (the pipe the path loads),
     # and the DFMA-chain probe measured in this run beside it
@@ -378,7 +393,8 @@ def bench_ours(args):
     # ---- end to end through the C ABI with host buffers
     host = {k: torch.from_numpy(getattr(pb, k)).pin_memory()
             for k in ("mats", "mat_off", "k", "l", "row_mult", "row_off", "col_mult", "col_off")}
-    out_host = torch.empty(pb.batch, dtype=torch.complex128).pin_memory()
+    out_host = torch.empty(full.batch if split else pb.batch,
+                           dtype=torch.complex128).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in host.values())
     d2h = out_host.numel() * out_host.element_size()
 
@@ -387,7 +403,8 @@ def bench_ours(args):
             for k, t in host.items():
                 getattr(db, k).copy_(t, non_blocking=True)
             api.permanent_batched(db, plan, out=out, stream=stream)
-            out_host.copy_(out, non_blocking=True)
+            res = api.gather_partitioned(out, rank_of) if split else out
+            out_host.copy_(res, non_blocking=True)
         stream.synchronize()
 
     for _ in range(2):
@@ -427,9 +444,10 @@ def bench_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
         "config": bench_config(WORKLOAD if args.workload == "ragged" else workload_desc,
-                               int(job_perms), int(job_terms), world),
+                               int(job_perms), int(job_terms), world, split),
         "method": "batched persistent kernel, CUDA graph, " + (
             f"chunks of about 2^{args.chunk_log2} terms" if args.chunk_log2 else
             "default chunks" if args.no_autotune else "autotuned chunks"),
@@ -747,9 +765,10 @@ def bench_reference(args):
     threads = host_cores()
     idx = oracle_sample(pb, args.cpu_sample_terms)
     terms = glynn_terms(pb, idx)
-    # the job the GPU arm measures: blocks 0 .. world-1 (the oracle times block 0)
+    # the job the GPU arm measures: blocks 0 .. world-1, or with --split block 0
+    # alone (the oracle times block 0)
     job_terms = glynn_terms(pb, range(pb.batch))
-    for blk in range(1, world):
+    for blk in range(1, 1 if args.split else world):
         bs = W.ragged(block=blk, sizes_only=True)
         job_terms += glynn_terms(bs, range(bs.batch))
     for _ in range(args.warmup):
@@ -760,9 +779,10 @@ def bench_reference(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference",
-        "config": bench_config(WORKLOAD, pb.batch * world, int(job_terms), world),
+        "scaling": "strong" if args.split and world > 1 else "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": bench_config(WORKLOAD, pb.batch * (1 if args.split else world),
+                               int(job_terms), world, args.split),
         "method": "CPU oracle: Ryser FP64 + double-double accumulation, all host cores",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{len(idx)} of {pb.batch} permanents per step "
@@ -789,6 +809,9 @@ def main(argv=None):
     ap.add_argument("--k", type=int, default=18,
                     help="hafnian profiling cases: base size k (N = 2k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split", action="store_true",
+                    help="with N > 1: split one batch over the ranks by whole permanents and "
+                         "all-gather the outputs (strong scaling) instead of one block per rank")
     ap.add_argument("--cpu-sample-terms", type=float, default=math.inf,
                     help="Ryser terms of the oracle sample (default: the whole batch, "
                          "about 2-3 s on 16 host cores; repeated to about 10 s)")

@@ -182,6 +182,22 @@ int pq_combine_partials(const double* parts, int32_t nshards, int64_t batch, con
 int pq_combine_partials_host(const double* parts, int32_t nshards, int64_t batch,
                              const int32_t* n, pq_c128* out);
 
+/* A batch split over ranks by whole permanents (independent problems need no
+ * exchange step; each rank evaluates its items with an ordinary plan and the
+ * outputs are gathered).  Items are taken largest first and each goes to the
+ * rank with the least work so far, ties to the lower rank; an item's work is
+ * its Gray-code term count times the algorithmic flops per term of the
+ * forward pass (2l + 6(n-1) + 2, +2 for weighted codes), which the forward
+ * kernel's time follows.  sz: the batch's sizes (host, as for
+ * pq_plan_create; mat_off is not read).  rank_of_item: host, batch entries,
+ * written with each item's rank in [0, ranks).  terms_per_rank: host, ranks
+ * entries, written with the Gray-code terms each rank sums.  The result
+ * depends only on the sizes, so every rank computes the same partition.
+ * Host only, no GPU.  Errors: PQ_ERR_ARG (null, ranks outside [1, 65536],
+ * negative sizes or offsets), PQ_ERR_UNSUPPORTED (as pq_plan_create). */
+int pq_partition_batch(const pq_batch_sizes* sizes, int32_t ranks, int32_t* rank_of_item,
+                       int64_t* terms_per_rank);
+
 /* Boson-sampling probabilities, Eq. (BS_prob).  U: device, m x m, U[out][in];
  * input_occ: device, m; output_occ: device, B x m; probs: device, B doubles;
  * amps: device, B complex, nullable -- receives per(U_{s,t}) (needed by the

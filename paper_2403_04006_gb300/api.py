@@ -228,6 +228,66 @@ def permanent_distributed(db: DeviceBatch, plan: Plan, group=None, stream=None) 
     return torch.from_numpy(combine_partials([p.numpy() for p in parts], n))
 
 
+def partition_batch(pb: PermBatch, ranks: int) -> tuple[np.ndarray, np.ndarray]:
+    """The library's balanced split of a batch over ``ranks`` ranks by whole
+    permanents (pq_partition_batch): the rank of every item and the Gray-code
+    terms of every rank.  Host only; every rank computes the same split."""
+    keep = [np.ascontiguousarray(x) for x in
+            (pb.mat_off, pb.k, pb.l, pb.row_mult, pb.row_off, pb.col_mult, pb.col_off)]
+    s = _pq.pq_batch_sizes()
+    s.batch = pb.batch
+    s.mat_off, s.k, s.l, s.row_mult, s.row_off, s.col_mult, s.col_off = [
+        x.ctypes.data if x.size else None for x in keep]
+    return _pq.pq_partition_batch(s, ranks)
+
+
+def gather_partitioned(local: torch.Tensor, rank_of: np.ndarray, group=None) -> torch.Tensor:
+    """The outputs of a batch split by ``partition_batch``, in item order, on
+    every rank: rank r holds the outputs of its items (ascending item index)
+    in ``local``; one all_gather of equal-length padded buffers, no
+    arithmetic.  The result lives on the device of ``local`` with NCCL, on
+    the CPU otherwise.  Without an initialised process group ``local`` is the
+    whole batch."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return local
+    world = dist.get_world_size(group)
+    counts = np.bincount(rank_of, minlength=world)
+    t = local if dist.get_backend(group) == "nccl" else local.cpu()
+    width = int(counts.max()) if counts.size else 0
+    pad = torch.zeros(width, dtype=t.dtype, device=t.device)
+    pad[:t.numel()] = t
+    bufs = [torch.empty_like(pad) for _ in range(world)]
+    dist.all_gather(bufs, pad, group=group)
+    out = torch.empty(len(rank_of), dtype=t.dtype, device=t.device)
+    for r in range(world):
+        idx = torch.from_numpy(np.nonzero(rank_of == r)[0]).to(t.device)
+        out[idx] = bufs[r][:int(counts[r])]
+    return out
+
+
+def permanent_partitioned(pb: PermBatch, device, group=None, use_graph: bool = False,
+                          stream=None) -> torch.Tensor:
+    """Permanents of a batch split over the ranks of a process group by whole
+    permanents: this rank plans and evaluates its items of
+    ``partition_batch(pb, world)`` and every rank gets all outputs in item
+    order (``gather_partitioned``)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        rank, world = dist.get_rank(group), dist.get_world_size(group)
+    else:
+        rank, world = 0, 1
+    rank_of, _ = partition_batch(pb, world)
+    sub = pb.subset(np.nonzero(rank_of == rank)[0])
+    db = DeviceBatch(sub, device)
+    plan = Plan.for_batch(sub, use_graph=use_graph)
+    local = permanent_batched(db, plan, stream=stream)
+    if stream is not None:
+        stream.synchronize()
+    plan.close()
+    return gather_partitioned(local, rank_of, group)
+
+
 def permanent_backward(db: DeviceBatch, grad_out: torch.Tensor, plan: Plan | None = None,
                        mats: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     m = db.mats if mats is None else mats

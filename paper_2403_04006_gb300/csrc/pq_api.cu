@@ -15,6 +15,7 @@
 #include <cstring>
 #include <mutex>
 #include <numeric>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -671,6 +672,23 @@ static int plan_common_init(pq_plan* P, const pq_plan_options* opts)
     return PQ_OK;
 }
 
+// The size arrays a batch needs: all of them for a non-empty batch, except
+// that the multiplicity arrays may be null when every item has no rows
+// (row_mult) or no columns (col_mult), as a batch of n = 0 items has.
+static bool sizes_present(const pq_batch_sizes* sz, bool need_mat_off)
+{
+    if (sz->batch <= 0)
+        return true;
+    if (!sz->k || !sz->l || !sz->row_off || !sz->col_off || (need_mat_off && !sz->mat_off))
+        return false;
+    bool rows = false, cols = false;
+    for (int64_t b = 0; b < sz->batch; ++b) {
+        rows = rows || sz->k[b] > 0;
+        cols = cols || sz->l[b] > 0;
+    }
+    return (!rows || sz->row_mult) && (!cols || sz->col_mult);
+}
+
 extern "C" int pq_plan_create(const pq_batch_sizes* sz, const pq_plan_options* opts,
                               pq_plan** out)
 {
@@ -679,8 +697,7 @@ extern "C" int pq_plan_create(const pq_batch_sizes* sz, const pq_plan_options* o
     *out = nullptr;
     if (sz->batch < 0)
         return fail(PQ_ERR_ARG, "negative batch");
-    if (sz->batch > 0 && (!sz->mat_off || !sz->k || !sz->l || !sz->row_mult || !sz->row_off ||
-                          !sz->col_mult || !sz->col_off))
+    if (!sizes_present(sz, true))
         return fail(PQ_ERR_ARG, "null size array");
     if (sz->batch > (int64_t(1) << 30))
         return fail(PQ_ERR_UNSUPPORTED, "batch above 2^30");
@@ -1708,6 +1725,60 @@ extern "C" int pq_plan_item_info(int32_t k, int32_t l, const int32_t* row_mult,
     for (size_t d = 0; d < it.drow.size() && d < (size_t)PQ_MAX_N; ++d) {
         out->radix[d] = it.drad[d];
         out->row_of_digit[d] = it.drow[d];
+    }
+    return PQ_OK;
+}
+
+// ---------------------------------------------------------------- batch partition
+// Largest work first, each to the rank with the least work so far (ties: the
+// lower rank); work = Gray-code terms x algorithmic flops per term, the
+// quantity the forward kernel's time follows.  Host only.
+extern "C" int pq_partition_batch(const pq_batch_sizes* sz, int32_t ranks, int32_t* rank_of_item,
+                                  int64_t* terms_per_rank)
+{
+    if (!sz || !terms_per_rank || (sz->batch > 0 && !rank_of_item))
+        return fail(PQ_ERR_ARG, "null argument");
+    if (ranks < 1 || ranks > 65536)
+        return fail(PQ_ERR_ARG, "ranks %d outside [1, 65536]", ranks);
+    if (sz->batch < 0)
+        return fail(PQ_ERR_ARG, "negative batch");
+    if (!sizes_present(sz, false))
+        return fail(PQ_ERR_ARG, "null size array");
+    if (sz->batch > (int64_t(1) << 30))
+        return fail(PQ_ERR_UNSUPPORTED, "batch above 2^30");
+    const int64_t nb = sz->batch;
+    std::vector<double> work(nb);
+    std::vector<int64_t> terms(nb);
+    for (int64_t b = 0; b < nb; ++b) {
+        if (sz->row_off[b] < 0 || sz->col_off[b] < 0)
+            return fail(PQ_ERR_ARG, "negative offset at item %lld", (long long)b);
+        ItemPlan it;
+        const int rc = build_item(sz->row_mult + sz->row_off[b], sz->col_mult + sz->col_off[b],
+                                  sz->k[b], sz->l[b], 0, sz->l[b], it);
+        if (rc != PQ_OK)
+            return fail(rc, "item %lld: %s", (long long)b, g_err.c_str());
+        terms[b] = it.trivial ? 0 : it.T;
+        work[b] = it.trivial ? 1.0 : (double)it.T * fwd_flops_per_term(it);
+    }
+    std::vector<int64_t> order(nb);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return work[a] > work[b]; });
+    // min-heap of (work so far, rank)
+    using Load = std::pair<double, int32_t>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int32_t r = 0; r < ranks; ++r) {
+        heap.push({0.0, r});
+        terms_per_rank[r] = 0;
+    }
+    for (int64_t q = 0; q < nb; ++q) {
+        const int64_t b = order[q];
+        Load top = heap.top();
+        heap.pop();
+        rank_of_item[b] = top.second;
+        terms_per_rank[top.second] += terms[b];
+        top.first += work[b];
+        heap.push(top);
     }
     return PQ_OK;
 }

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "pq_lossy_plan_create": (_i32, [_i32, _vp, _vp, _i64, ctypes.POINTER(_vp)]),
     "pq_lossy_plan_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pq_lossy_plan_destroy": (_i32, [_vp]),
+    "pq_partition_batch": (_i32, [ctypes.POINTER(pq_batch_sizes), _i32, _vp, _vp]),
     "pq_sampler_plan_create": (_i32, [_i32, _vp, _i64, ctypes.POINTER(_vp)]),
     "pq_sampler_plan_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pq_sampler_plan_destroy": (_i32, [_vp]),
@@ -157,6 +158,17 @@ def pq_plan_create(sizes: pq_batch_sizes, opts: pq_plan_options | None = None) -
                                          ctypes.byref(opts) if opts else None,
                                          ctypes.byref(out)), "pq_plan_create")
     return out.value
+
+
+def pq_partition_batch(sizes: pq_batch_sizes, ranks: int) -> tuple[np.ndarray, np.ndarray]:
+    """(rank of every item, Gray-code terms per rank) of the balanced split."""
+    rank_of = np.zeros(max(int(sizes.batch), 0), dtype=np.int32)
+    terms = np.zeros(max(int(ranks), 0), dtype=np.int64)
+    _check(load_library().pq_partition_batch(ctypes.byref(sizes), int(ranks),
+                                             rank_of.ctypes.data if rank_of.size else None,
+                                             terms.ctypes.data if terms.size else None),
+           "pq_partition_batch")
+    return rank_of, terms
 
 
 def pq_plan_create_bs(m: int, input_occ: np.ndarray, output_occ: np.ndarray, B: int,

@@ -220,3 +220,29 @@ def test_tune_cache_under_the_current_device_name(dev, tmp_path):
         assert abs(got - ref) <= 1e-10 * abs(ref)
     finally:
         pq.pq_tune_table_set(saved)
+
+
+def test_partitioned_batch_matches_the_whole(dev):
+    """The items of each rank of a 3-way partition (pq_partition_batch),
+    evaluated one rank after another on this GPU and put back in item order,
+    give the whole batch's permanents (a smaller batch may cut its Gray codes
+    into other chunks, so to 1e-11 relative) and the oracle's; without a
+    process group the partitioned call evaluates the whole batch."""
+    items = small_items(36, count=60, nmax=14)
+    items.append((np.zeros((0, 0)), [], []))
+    pb = W.pack_batch(items)
+    whole = api.permanent_batched(api.DeviceBatch(pb, dev), api.Plan.for_batch(pb)).cpu().numpy()
+    rank_of, terms = api.partition_batch(pb, 3)
+    assert (np.bincount(rank_of, minlength=3) > 0).all()
+    got = np.full(pb.batch, complex(7.0, 7.0))
+    for r in range(3):
+        idx = np.nonzero(rank_of == r)[0]
+        sub = pb.subset(idx)
+        got[idx] = api.permanent_batched(api.DeviceBatch(sub, dev),
+                                         api.Plan.for_batch(sub)).cpu().numpy()
+    assert np.all(np.abs(got - whole) <= 1e-11 * np.abs(whole))
+    for b, (B, r, c) in enumerate(items):
+        ref = O.perm_ryser(B, r, c, gold=True)
+        assert abs(got[b] - ref) <= 1e-10 * abs(ref), b
+    solo = api.permanent_partitioned(pb, dev).cpu().numpy()
+    assert np.all(np.abs(solo - whole) <= 1e-11 * np.abs(whole))
