@@ -99,6 +99,12 @@ typedef struct {
 #define PQ_METHOD_BATCHED 0 /* one persistent launch for the whole batch (default)   */
 #define PQ_METHOD_PLAIN 1   /* one launch per permanent, issued back to back          */
 
+/* Where a lane keeps its column sums in the forward walk. */
+#define PQ_SUMS_AUTO 0      /* the planner's choice (default)                            */
+#define PQ_SUMS_SHARED 1    /* shared memory, lane-major: any product side               */
+#define PQ_SUMS_REGISTERS 2 /* registers: product sides of at most 20 columns (the plan
+                               falls back to shared memory for wider ones)              */
+
 /* Plan options; zero-initialise and set what you need. */
 typedef struct {
     int32_t method;          /* PQ_METHOD_*                                              */
@@ -110,7 +116,7 @@ typedef struct {
     int32_t shard_index;     /* with shard_count > 1: this plan covers shard shard_index  */
     int32_t shard_count;     /* of the warp tasks of every permanent (see
                                 pq_permanent_partials); 0 or 1: no sharding              */
-    int32_t reserved;
+    int32_t column_sums;     /* PQ_SUMS_*                                                 */
 } pq_plan_options;
 
 /* Opaque plan: the host-side schedule of one batch shape (which side of each
@@ -451,7 +457,8 @@ typedef struct {
     int64_t launches_forward;
     int64_t launches_backward;
     int32_t lmax;
-    int32_t reserved;
+    int32_t column_sums; /* where the forward walk keeps them: PQ_SUMS_SHARED or
+                            PQ_SUMS_REGISTERS (the planner's choice under AUTO)    */
     double fp64_instr_forward;
     double fp64_instr_backward;
     double fp64_instr_forward_executed;

@@ -27,9 +27,15 @@ def _ptr(t: torch.Tensor | None):
     return t.data_ptr()
 
 
+_SUMS = {"auto": _pq.PQ_SUMS_AUTO, "shared": _pq.PQ_SUMS_SHARED,
+         "registers": _pq.PQ_SUMS_REGISTERS}
+
+
 def _opts(method: str, use_graph: bool, chunk_log2: int, warps_per_block: int = 0,
-          blocks_per_sm: int = 0, shard: tuple[int, int] | None = None) -> _pq.pq_plan_options:
+          blocks_per_sm: int = 0, shard: tuple[int, int] | None = None,
+          column_sums: str = "auto") -> _pq.pq_plan_options:
     o = _pq.pq_plan_options()
+    o.column_sums = _SUMS[column_sums]
     o.method = {"batched": _pq.PQ_METHOD_BATCHED, "plain": _pq.PQ_METHOD_PLAIN}[method]
     o.use_graph = 1 if use_graph else 0
     o.chunk_log2 = int(chunk_log2)
@@ -93,9 +99,11 @@ class Plan:
     @classmethod
     def for_batch(cls, pb: PermBatch | DeviceBatch, method: str = "batched",
                   use_graph: bool = False, chunk_log2: int = 0, warps_per_block: int = 0,
-                  blocks_per_sm: int = 0, shard: tuple[int, int] | None = None) -> "Plan":
+                  blocks_per_sm: int = 0, shard: tuple[int, int] | None = None,
+                  column_sums: str = "auto") -> "Plan":
         """Plan a ragged batch; ``shard=(index, count)`` makes a plan for one
-        shard of every permanent's warp tasks (see ``permanent_partials``)."""
+        shard of every permanent's warp tasks (see ``permanent_partials``);
+        ``column_sums`` is "auto", "shared" or "registers" (PQ_SUMS_*)."""
         db = pb if isinstance(pb, DeviceBatch) else None
         host = db.host if db is not None else pb
         keep = [np.ascontiguousarray(x) for x in
@@ -106,23 +114,25 @@ class Plan:
         s.mat_off, s.k, s.l, s.row_mult, s.row_off, s.col_mult, s.col_off = [
             x.ctypes.data if x.size else None for x in keep]
         h = _pq.pq_plan_create(s, _opts(method, use_graph, chunk_log2, warps_per_block,
-                                        blocks_per_sm, shard))
+                                        blocks_per_sm, shard, column_sums))
         return cls(h, "batch")
 
     @classmethod
     def for_bs(cls, m: int, s, t, method: str = "batched", use_graph: bool = False,
                chunk_log2: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0,
-               shard: tuple[int, int] | None = None) -> "Plan":
+               shard: tuple[int, int] | None = None, column_sums: str = "auto") -> "Plan":
         s = np.ascontiguousarray(np.asarray(s, dtype=np.int32))
         t = np.ascontiguousarray(np.asarray(t, dtype=np.int32).reshape(-1, m))
         h = _pq.pq_plan_create_bs(int(m), s, t, int(t.shape[0]),
                                   _opts(method, use_graph, chunk_log2, warps_per_block,
-                                        blocks_per_sm, shard))
+                                        blocks_per_sm, shard, column_sums))
         return cls(h, "bs")
 
     def stats(self) -> dict:
         st = _pq.pq_plan_get_stats(self.handle)
-        return {f: getattr(st, f) for f, _ in _pq.pq_plan_stats._fields_ if f != "reserved"}
+        d = {f: getattr(st, f) for f, _ in _pq.pq_plan_stats._fields_}
+        d["column_sums"] = {v: k for k, v in _SUMS.items()}[d["column_sums"]]
+        return d
 
     def autotune(self, db: DeviceBatch | None = None, U: torch.Tensor | None = None,
                  stream=None):

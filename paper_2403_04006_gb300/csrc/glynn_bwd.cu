@@ -853,7 +853,7 @@ __device__ void bwdr_task(const BwdArgs& a, const Task& t, BwdRegSmem& sm, int& 
 // class bound); the guards are those of the kernel above, without a bound on
 // the repeated columns.
 template <int NL>
-__global__ void __launch_bounds__(256) glynn_bwd_reg_kernel(BwdArgs a, int64_t t_begin,
+__global__ void __launch_bounds__(256, 1) glynn_bwd_reg_kernel(BwdArgs a, int64_t t_begin,
                                                             int64_t t_end, int kmax, int jb,
                                                             int queue)
 {

@@ -63,8 +63,9 @@ struct WarpSmem {
 
 // Copy the oriented base matrix of permanent D into shared memory and form
 // base_j = sum_i r_i b_ij (all Gray digits at zero).
-__device__ void stage_perm(const ExecArgs& a, const PermDesc& D, const MetaView& mv,
-                           WarpSmem& sm, int lane)
+template <class SM>
+__device__ void stage_perm(const ExecArgs& a, const PermDesc& D, const MetaView& mv, SM& sm,
+                           int lane)
 {
     const int k = D.k, l = D.l;
     for (int e = lane; e < k * l; e += kWarp) {
@@ -195,6 +196,8 @@ __device__ __forceinline__ void finalize(const ExecArgs& a, const PermDesc& D, d
         a.out_prob[D.out] = (re * re + im * im) * D.norm;
 }
 
+__device__ void combine_task(const ExecArgs& a, const Task& t, const PermDesc& D, dd2 res, int lane);
+
 __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int& staged, int lane)
 {
     const PermDesc D = a.desc[t.perm];
@@ -307,8 +310,14 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
         res.il = il;
         res = warp_sum_dd2(res);
     }
+    combine_task(a, t, D, res, lane);
+}
 
-    // ---- combine tasks of this permanent
+// The task's sum res (the same on every lane) goes to the permanent's output
+// if the permanent has one task; otherwise to its slot, and the warp that
+// writes the last slot adds the slots in task order.
+__device__ void combine_task(const ExecArgs& a, const Task& t, const PermDesc& D, dd2 res, int lane)
+{
     if (D.ntasks <= 1) {
         if (lane == 0)
             finalize(a, D, res);
@@ -338,6 +347,304 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
     tot = warp_sum_dd2(tot);
     if (lane == 0)
         finalize(a, D, tot);
+}
+
+// ---------------------------------------------------------------- register-resident walk
+// For product sides of at most kFwdRegMaxLd columns a lane keeps its column
+// sums in registers, in a walk instantiated for even column bounds NL and
+// launched once per class of permanents (at most NL product columns).
+// Columns 0 .. l-2 live in registers 0 .. l-2 and the last column l-1 in
+// register NL-1; the registers between are padding whose sum stays exactly
+// 1 + 0i (its base-matrix entries are staged as zeros and its extra-prefix
+// count as 0).  So no FP64 instruction of the walk depends on l: every column
+// loop runs over all NL registers without a test, and a padding column costs
+// its products by 1, which are exact (a test per column made the compiler
+// predicate the FP64 work, and predicated-off instructions took 40-55% of
+// the FP64 pipe).  The products are formed in the order of the shared-memory
+// walk, so both give the same bits.  A warp's shared memory holds the base
+// matrix and its column sums in register order and the small integer arrays.
+__host__ __device__ inline int reg_warp_smem_bytes(int kmax, int ld)
+{
+    int bytes = (kmax * ld + ld) * 16 + (16 + ld) * 4;
+    return (bytes + 15) & ~15;
+}
+
+struct RegSmem {
+    double2* M;       // kmax x ld, register order
+    double2* base;    // ld, register order
+    int32_t* lowrow;  // 16
+    int32_t* ecnt;    // ld, register order
+    int ld;
+    __device__ RegSmem(unsigned char* raw, int kmax, int ld_)
+    {
+        ld = ld_;
+        M = reinterpret_cast<double2*>(raw);
+        base = M + kmax * ld;
+        lowrow = reinterpret_cast<int32_t*>(base + ld);
+        ecnt = lowrow + 16;
+    }
+};
+
+// Register of product column j of a permanent with l columns.
+template <int NL>
+__device__ __forceinline__ int reg_of(int j, int l)
+{
+    return j == l - 1 ? NL - 1 : j;
+}
+
+// Stage permanent D for the register walk: base matrix and base column sums
+// in register order (padding: entries 0, sum 1 + 0i), extra-prefix counts in
+// register order (padding: 0).  sm.ld = NL.
+template <int NL>
+__device__ void stage_perm_reg(const ExecArgs& a, const PermDesc& D, const MetaView& mv,
+                               RegSmem& sm, int lane)
+{
+    const int k = D.k, l = D.l;
+    for (int e = lane; e < k * NL; e += kWarp) {
+        const int i = e / NL, r = e - i * NL;
+        double2 v = make_double2(0.0, 0.0);
+        const int j = r == NL - 1 ? l - 1 : r;
+        if (r == NL - 1 || r < l - 1) {
+            const int64_t off =
+                D.src_off + (int64_t)mv.ridx[i] * D.si + (int64_t)mv.cidx[j] * D.sj;
+            v = a.src[off];
+        }
+        sm.M[e] = v;
+    }
+    for (int d = lane; d < D.J; d += kWarp)
+        sm.lowrow[d] = mv.drow[d];
+    for (int r = lane; r < NL; r += kWarp)
+        sm.ecnt[r] = r == NL - 1 ? mv.ecnt[l - 1] : (r < l - 1 ? mv.ecnt[r] : 0);
+    __syncwarp();
+    for (int r = lane; r < NL; r += kWarp) {
+        double2 s = make_double2(0.0, 0.0);
+        if (r == NL - 1 || r < l - 1) {
+            for (int i = 0; i < k; ++i) {
+                const double rm = (double)mv.rmul[i];
+                const double2 b = sm.M[i * NL + r];
+                s.x = __fma_rn(rm, b.x, s.x);
+                s.y = __fma_rn(rm, b.y, s.y);
+            }
+        } else {
+            s = make_double2(1.0, 0.0);
+        }
+        sm.base[r] = s;
+    }
+    __syncwarp();
+}
+
+// S += coef * (row Mr), every register (padding entries are zero).
+template <int NL>
+__device__ __forceinline__ void reg_add_row(double2 (&S)[NL], const double2* Mr, double coef)
+{
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+        const double2 b = Mr[r];
+        S[r].x = __fma_rn(coef, b.x, S[r].x);
+        S[r].y = __fma_rn(coef, b.y, S[r].y);
+    }
+}
+
+// One term, as glynn_term: acc +-= prod_j S_j^{c_j}.  jr = register of the
+// first column with an extra prefix (-1: every c_j = 1); ec = extra-prefix
+// counts in register order.
+template <int NL, bool NEG>
+__device__ __forceinline__ void reg_term(const double2 (&S)[NL], int jr, const int (&ec)[NL],
+                                         double2& acc)
+{
+    if (jr < 0) {
+        double2 p = S[0];
+#pragma unroll
+        for (int r = 1; r < NL - 1; ++r)
+            p = cmul(p, S[r]);
+        cfma_acc<NEG>(acc, p, S[NL - 1]);
+        return;
+    }
+    // P(q) = S_0 ... S_{q-1} for every column; at the first column with an
+    // extra prefix ex starts as that prefix, and each extra multiplies it in
+    double2 pre = S[0], ex = S[0];
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+        if (r > 0)
+            pre = cmul(pre, S[r]);
+        ex = r == jr ? pre : ex;
+        const int e0 = r == jr ? 1 : 0;
+#pragma unroll 1
+        for (int e = e0; e < ec[r]; ++e)
+            ex = cmul(ex, pre);
+    }
+    cfma_acc<NEG>(acc, pre, ex);
+}
+
+// One Gray step, as glynn_step, on the register column sums.
+template <int NL>
+__device__ __forceinline__ bool reg_step(LowWalk& wk, const RegSmem& sm, double2 (&S)[NL])
+{
+    int up;
+    const int d = low_step(wk, up);
+    reg_add_row(S, sm.M + sm.lowrow[d] * NL, up > 0 ? -2.0 : 2.0);
+    return ((wk.radm1 >> (4 * d)) & 15u) > 1u;
+}
+
+// The walk of this lane's chunk c (as in process_task); returns the lane's
+// double-double sum times its high-digit weight, before the lane reduction.
+template <int NL>
+__device__ __forceinline__ dd2 reg_walk(const PermDesc& D, const MetaView& mv, const RegSmem& sm,
+                                        int64_t c, bool active)
+{
+    const int l = D.l, J = D.J, ndig = D.ndig;
+    double2 S[NL];
+    int ec[NL];
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+        S[r] = sm.base[r];
+        ec[r] = sm.ecnt[r];
+    }
+    const int jr = D.jf < 0 ? -1 : reg_of<NL>(D.jf, l);
+    uint64_t whigh_u = 1;
+    int gpar = 0;
+#pragma unroll 1
+    for (int d = J; d < ndig; ++d) {
+        const int rad = mv.drad[d];
+        const int g = (int)(c % rad);
+        c /= rad;
+        if (g == 0)
+            continue;
+        reg_add_row(S, sm.M + mv.drow[d] * NL, (double)(-2 * g));
+        whigh_u *= binom_u64(mv.dtop[d], g);
+        gpar += g;
+    }
+    double whigh = active ? (double)whigh_u : 0.0;
+    if (gpar & 1)
+        whigh = -whigh;
+
+    LowWalk wk;
+    wk.v = 0;
+    wk.g = 0;
+    wk.dir = 0;
+    wk.radm1 = 0;
+    wk.topp = 0;
+    for (int d = 0; d < J; ++d) {
+        wk.radm1 |= uint64_t(mv.drad[d] - 1) << (4 * d);
+        wk.topp |= uint64_t(mv.dtop[d]) << (4 * d);
+    }
+    const bool weighted = D.weighted != 0;
+    double wlow = 1.0;
+    double2 acc = make_double2(0.0, 0.0), run = make_double2(0.0, 0.0);
+    double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+    const int64_t L = D.L;
+    int64_t s = 0;
+    int blk = 0;
+#pragma unroll 1
+    while (s < L) {
+        reg_term<NL, false>(S, jr, ec, acc);
+        if (++s < L) {
+            if (reg_step(wk, sm, S) && weighted)
+                reweight(wk, J, wlow, acc, run);
+            reg_term<NL, true>(S, jr, ec, acc);
+            if (++s < L && reg_step(wk, sm, S) && weighted)
+                reweight(wk, J, wlow, acc, run);
+        }
+        if (++blk == 16) {
+            blk = 0;
+            if (weighted) {
+                run.x = __fma_rn(wlow, acc.x, run.x);
+                run.y = __fma_rn(wlow, acc.y, run.y);
+                acc = run;
+                run = make_double2(0.0, 0.0);
+            }
+            dd_acc(rh, rl, acc.x);
+            dd_acc(ih, il, acc.y);
+            acc = make_double2(0.0, 0.0);
+        }
+    }
+    if (weighted) {
+        run.x = __fma_rn(wlow, acc.x, run.x);
+        run.y = __fma_rn(wlow, acc.y, run.y);
+        acc = run;
+    }
+    dd_acc(rh, rl, acc.x);
+    dd_acc(ih, il, acc.y);
+    fast_two_sum(rh, rl, rh, rl);
+    fast_two_sum(ih, il, ih, il);
+    dd_mul_d(rh, rl, whigh);
+    dd_mul_d(ih, il, whigh);
+    dd2 res;
+    res.rh = rh;
+    res.rl = rl;
+    res.ih = ih;
+    res.il = il;
+    return res;
+}
+
+template <int NL>
+__device__ void process_task_reg(const ExecArgs& a, const Task& t, RegSmem& sm, int& staged,
+                                 int lane)
+{
+    const PermDesc D = a.desc[t.perm];
+    const MetaView mv = meta_view(a.meta, D);
+    dd2 res = {0.0, 0.0, 0.0, 0.0};
+    if (!D.trivial) {
+        if (staged != t.perm) {
+            __syncwarp();
+            stage_perm_reg<NL>(a, D, mv, sm, lane);
+            staged = t.perm;
+        }
+        const int64_t chunk0 = (int64_t)t.part * kWarp;
+        const bool active = chunk0 + lane < D.nchunks;
+        res = reg_walk<NL>(D, mv, sm, active ? (chunk0 + lane) : 0, active);
+        res = warp_sum_dd2(res);
+    }
+    combine_task(a, t, D, res, lane);
+}
+
+// The register-resident kernel of column bound NL: tasks as in
+// glynn_fwd_kernel, each of a permanent with at most NL product columns (a
+// task beyond that is skipped and recorded as a layout error).  The batched
+// method launches one such kernel per column class, so that the warps of an
+// SM run one instantiation of the walk: warps running different ones (a
+// single kernel dispatching on l) ran 1.6 times slower.
+template <int NL>
+__global__ void __launch_bounds__(256, 1) glynn_fwd_reg_kernel(ExecArgs a, int64_t t_begin,
+                                                             int64_t t_end, int kmax, int ld,
+                                                             int queue)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (NL > ld) {  // the launch's shared-memory rows are narrower than this class's
+        if (threadIdx.x == 0)
+            record_error(a.err, kErrDescLayout, t_begin);
+        return;
+    }
+    RegSmem sm(smem_raw + warp * reg_warp_smem_bytes(kmax, ld), kmax, NL);
+    int staged = -1;
+    auto run = [&](int64_t ti) {
+        const Task t = a.tasks[ti];
+        const int32_t bad = task_guard(t, a.desc, a.nperm, a.nmeta, a.nslots, kmax,
+                                       ld < NL ? ld : NL, kMaxLowDigits);
+        if (bad) {
+            if (lane == 0)
+                record_error(a.err, bad, ti);
+            return;
+        }
+        process_task_reg<NL>(a, t, sm, staged, lane);
+    };
+    if (!queue) {
+        const int64_t ti = t_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+        if (ti < t_end)
+            run(ti);
+        return;
+    }
+    for (;;) {
+        int q = 0;
+        if (lane == 0)
+            q = atomicAdd(a.counters, 1);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        const int64_t ti = t_begin + q;
+        if (ti >= t_end)
+            break;
+        run(ti);
+    }
 }
 
 // Task ti of the list, once its guards pass (a failing task is skipped and
@@ -385,6 +692,74 @@ __global__ void __launch_bounds__(256) glynn_fwd_kernel(ExecArgs a, int64_t t_be
     }
 }
 
+// All column classes in one persistent launch: each task runs the
+// instantiation of its own class.
+__global__ void __launch_bounds__(256, 1) glynn_fwd_reg_mixed_kernel(ExecArgs a, int64_t t_begin,
+                                                                     int64_t t_end, int kmax,
+                                                                     int ld, int queue)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* raw = smem_raw + warp * reg_warp_smem_bytes(kmax, ld);
+    int staged = -1, staged_nl = 0;
+    auto run = [&](int64_t ti) {
+        const Task t = a.tasks[ti];
+        const int32_t bad =
+            task_guard(t, a.desc, a.nperm, a.nmeta, a.nslots, kmax, ld, kMaxLowDigits);
+        if (bad) {
+            if (lane == 0)
+                record_error(a.err, bad, ti);
+            return;
+        }
+        const int l = a.desc[t.perm].l;
+        const int nl = l <= 4 ? 4 : l + (l & 1);
+        if (nl > ld) {  // the class's rows do not fit the launch's layout
+            if (lane == 0)
+                record_error(a.err, kErrDescLayout, ti);
+            return;
+        }
+        if (nl != staged_nl)
+            staged = -1;  // the staged layout depends on the class
+        staged_nl = nl;
+        switch (nl) {
+#define PQ_REG_CASE(N)                                   \
+    case N: {                                            \
+        RegSmem sm(raw, kmax, N);                        \
+        process_task_reg<N>(a, t, sm, staged, lane);     \
+        break;                                           \
+    }
+            PQ_REG_CASE(4)
+            PQ_REG_CASE(6)
+            PQ_REG_CASE(8)
+            PQ_REG_CASE(10)
+            PQ_REG_CASE(12)
+            PQ_REG_CASE(14)
+            PQ_REG_CASE(16)
+            PQ_REG_CASE(18)
+            PQ_REG_CASE(20)
+#undef PQ_REG_CASE
+        default:
+            break;
+        }
+    };
+    if (!queue) {
+        const int64_t ti = t_begin + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+        if (ti < t_end)
+            run(ti);
+        return;
+    }
+    for (;;) {
+        int q = 0;
+        if (lane == 0)
+            q = atomicAdd(a.counters, 1);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        const int64_t ti = t_begin + q;
+        if (ti >= t_end)
+            break;
+        run(ti);
+    }
+}
+
 // ---------------------------------------------------------------- host side
 int fwd_smem_per_warp(int kmax, int ld) { return warp_smem_bytes(kmax, ld); }
 
@@ -423,6 +798,101 @@ cudaError_t fwd_launch_plain(int ld, const ExecArgs& a, int64_t t_begin, int64_t
     const int64_t nt = t_end - t_begin;
     const unsigned grid = (unsigned)((nt + wpb - 1) / wpb);
     glynn_fwd_kernel<<<grid, 32 * wpb, smem, st>>>(a, t_begin, t_end, kmax, ld, 0);
+    return cudaGetLastError();
+}
+
+// ---- register-resident walk
+int fwd_reg_class_of(int l) { return l <= 4 ? 4 : l + (l & 1); }
+
+int fwd_reg_smem_per_warp(int kmax, int ld) { return reg_warp_smem_bytes(kmax, ld); }
+
+static const void* fwd_reg_kernel_for(int nl)
+{
+    switch (nl) {
+    case 4: return (const void*)glynn_fwd_reg_kernel<4>;
+    case 6: return (const void*)glynn_fwd_reg_kernel<6>;
+    case 8: return (const void*)glynn_fwd_reg_kernel<8>;
+    case 10: return (const void*)glynn_fwd_reg_kernel<10>;
+    case 12: return (const void*)glynn_fwd_reg_kernel<12>;
+    case 14: return (const void*)glynn_fwd_reg_kernel<14>;
+    case 16: return (const void*)glynn_fwd_reg_kernel<16>;
+    case 18: return (const void*)glynn_fwd_reg_kernel<18>;
+    case 20: return (const void*)glynn_fwd_reg_kernel<20>;
+    default: return nullptr;
+    }
+}
+
+int fwd_reg_regs_per_thread(int nl)
+{
+    cudaFuncAttributes at{};
+    const void* f = fwd_reg_kernel_for(nl);
+    return (f && cudaFuncGetAttributes(&at, f) == cudaSuccess) ? at.numRegs : 255;
+}
+
+cudaError_t fwd_reg_prepare(int nl, int smem_bytes)
+{
+    const void* f = fwd_reg_kernel_for(nl);
+    if (!f)
+        return cudaErrorInvalidValue;
+    cudaFuncAttributes at{};
+    cudaError_t e = cudaFuncGetAttributes(&at, f);
+    if (e != cudaSuccess)
+        return e;
+    if (at.maxDynamicSharedSizeBytes >= smem_bytes)
+        return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+int fwd_reg_mixed_regs_per_thread()
+{
+    cudaFuncAttributes at{};
+    return cudaFuncGetAttributes(&at, glynn_fwd_reg_mixed_kernel) == cudaSuccess ? at.numRegs
+                                                                                : 255;
+}
+
+cudaError_t fwd_reg_mixed_prepare(int smem_bytes)
+{
+    cudaFuncAttributes at{};
+    cudaError_t e = cudaFuncGetAttributes(&at, glynn_fwd_reg_mixed_kernel);
+    if (e != cudaSuccess)
+        return e;
+    if (at.maxDynamicSharedSizeBytes >= smem_bytes)
+        return cudaSuccess;
+    return cudaFuncSetAttribute(glynn_fwd_reg_mixed_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+cudaError_t fwd_reg_mixed_launch(const ExecArgs& a, int64_t t_begin, int64_t t_end, int kmax,
+                                 int ld, unsigned grid, int wpb, int queue, cudaStream_t st)
+{
+    glynn_fwd_reg_mixed_kernel<<<grid, 32 * wpb, wpb * reg_warp_smem_bytes(kmax, ld), st>>>(
+        a, t_begin, t_end, kmax, ld, queue);
+    return cudaGetLastError();
+}
+
+template <int NL>
+static void fwd_reg_launch_nl(const ExecArgs& a, int64_t t_begin, int64_t t_end, int kmax, int ld,
+                              unsigned grid, int wpb, int queue, cudaStream_t st)
+{
+    glynn_fwd_reg_kernel<NL><<<grid, 32 * wpb, wpb * reg_warp_smem_bytes(kmax, ld), st>>>(
+        a, t_begin, t_end, kmax, ld, queue);
+}
+
+cudaError_t fwd_reg_launch(int nl, const ExecArgs& a, int64_t t_begin, int64_t t_end, int kmax,
+                           int ld, unsigned grid, int wpb, int queue, cudaStream_t st)
+{
+    switch (nl) {
+    case 4: fwd_reg_launch_nl<4>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    case 6: fwd_reg_launch_nl<6>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    case 8: fwd_reg_launch_nl<8>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    case 10: fwd_reg_launch_nl<10>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    case 12: fwd_reg_launch_nl<12>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    case 14: fwd_reg_launch_nl<14>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    case 16: fwd_reg_launch_nl<16>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    case 18: fwd_reg_launch_nl<18>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    case 20: fwd_reg_launch_nl<20>(a, t_begin, t_end, kmax, ld, grid, wpb, queue, st); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -414,6 +414,16 @@ static void free_plan_device(pq_plan* P)
 }
 
 // Chunks, tasks, descriptors, device upload.
+// Raise the dynamic shared-memory limit of the plan's forward kernel.
+static cudaError_t forward_prepare(const pq_plan* P)
+{
+    if (P->fwd_nl > 0)
+        return fwd_reg_prepare(P->fwd_nl, P->wpb * fwd_reg_smem_per_warp(P->kmax, P->fwd_ld));
+    if (P->fwd_nl < 0)
+        return fwd_reg_mixed_prepare(P->wpb * fwd_reg_smem_per_warp(P->kmax, P->fwd_ld));
+    return fwd_prepare(P->lmax, P->wpb * fwd_smem_per_warp(P->kmax, P->lmax));
+}
+
 static int schedule_and_upload(pq_plan* P)
 {
     P->uploaded = false;
@@ -440,12 +450,43 @@ static int schedule_and_upload(pq_plan* P)
     const int64_t plain_min = (int64_t)P->num_sms * 4 * kWarp;
     const int64_t plain_max = (int64_t)P->num_sms * 16 * 2 * kWarp;
 
+    // Where the walk keeps its column sums.  Registers pay when every
+    // permanent falls in one column class (m = 24 boson sampling, 4096
+    // patterns of 12 photons: 0.92 ms against 1.08 ms in shared memory); a
+    // batch that mixes classes runs one instantiation per class in one kernel,
+    // whose register count is that of the widest (226: 8 warps per SM), and
+    // was slower than shared memory (ragged batch: 24.6 ms against 22.7 ms),
+    // so the planner takes registers for a single class only, and a caller
+    // may ask for them (PQ_SUMS_REGISTERS) or for shared memory.
+    {
+        int cls = 0;
+        bool one = true;
+        for (const ItemPlan& it : P->items) {
+            if (it.trivial)
+                continue;
+            const int c = fwd_reg_class_of(it.l);
+            if (cls == 0)
+                cls = c;
+            else if (c != cls)
+                one = false;
+        }
+        const bool want = P->opts.column_sums == PQ_SUMS_REGISTERS ||
+                          (P->opts.column_sums == PQ_SUMS_AUTO && one);
+        P->fwd_nl = (want && P->lmax <= kFwdRegMaxLd) ? (one ? std::max(cls, 4) : -1) : 0;
+        P->fwd_ld = P->fwd_nl > 0   ? P->fwd_nl
+                    : P->fwd_nl < 0 ? fwd_reg_class_of(P->lmax)
+                                    : P->lmax;
+    }
     // launch geometry (it fixes the resident warps the batched cut is balanced for)
-    const int per_warp = fwd_smem_per_warp(P->kmax, P->lmax);
+    const int per_warp = P->fwd_nl != 0 ? fwd_reg_smem_per_warp(P->kmax, P->fwd_ld)
+                                        : fwd_smem_per_warp(P->kmax, P->lmax);
     if (per_warp > 200 * 1024)
         return fail(PQ_ERR_UNSUPPORTED, "shared memory per warp %d too large", per_warp);
     int wpb = 0, bps = 0;
-    launch_geometry(fwd_regs_per_thread(P->lmax), per_warp,
+    launch_geometry(P->fwd_nl > 0   ? fwd_reg_regs_per_thread(P->fwd_nl)
+                    : P->fwd_nl < 0 ? fwd_reg_mixed_regs_per_thread()
+                                    : fwd_regs_per_thread(P->lmax),
+                    per_warp,
                     P->opts.warps_per_block > 0 ? P->opts.warps_per_block : 8,
                     P->opts.blocks_per_sm > 0 ? P->opts.blocks_per_sm : 8, wpb, bps);
     P->wpb = wpb;
@@ -602,6 +643,7 @@ static int schedule_and_upload(pq_plan* P)
     P->stats.launches_forward = (P->opts.method == PQ_METHOD_PLAIN) ? np : 1;
     P->stats.launches_backward = (P->opts.method == PQ_METHOD_PLAIN) ? np + 1 : 2;
     P->stats.lmax = P->lmax;
+    P->stats.column_sums = P->fwd_nl != 0 ? PQ_SUMS_REGISTERS : PQ_SUMS_SHARED;
 
     // upload
     int rc;
@@ -624,7 +666,7 @@ static int schedule_and_upload(pq_plan* P)
         PQ_ALLOC(&P->err_d, 2 * sizeof(int32_t));
         PQ_CUDA(cudaMemset(P->err_d, 0, 2 * sizeof(int32_t)));
     }
-    cudaError_t e = fwd_prepare(P->lmax, P->wpb * per_warp);
+    cudaError_t e = forward_prepare(P);
     if (e != cudaSuccess)
         return fail(PQ_ERR_CUDA, "kernel attribute setup failed: %s", cudaGetErrorString(e));
     P->uploaded = true;
@@ -663,6 +705,8 @@ static int plan_common_init(pq_plan* P, const pq_plan_options* opts)
         return fail(PQ_ERR_ARG, "warps_per_block %d outside [0, 16]", P->opts.warps_per_block);
     if (P->opts.blocks_per_sm < 0 || P->opts.blocks_per_sm > 32)
         return fail(PQ_ERR_ARG, "blocks_per_sm %d outside [0, 32]", P->opts.blocks_per_sm);
+    if (P->opts.column_sums < PQ_SUMS_AUTO || P->opts.column_sums > PQ_SUMS_REGISTERS)
+        return fail(PQ_ERR_ARG, "column_sums %d is not a PQ_SUMS_* value", P->opts.column_sums);
     if (P->opts.shard_count < 0 || P->opts.shard_count > 65536 || P->opts.shard_index < 0 ||
         (P->opts.shard_count > 0 && P->opts.shard_index >= P->opts.shard_count) ||
         (P->opts.shard_count == 0 && P->opts.shard_index != 0))
@@ -875,14 +919,30 @@ static int run_forward_raw(pq_plan* P, const void* src, void* amps, double* prob
     if (P->opts.method == PQ_METHOD_PLAIN) {
         ExecArgs a = exec_args(P, src, amps, probs, false, partial);
         for (int64_t p = 0; p < P->nperm; ++p) {
-            cudaError_t e = fwd_launch_plain(P->lmax, a, P->plain_first[p], P->plain_first[p + 1],
-                                             P->kmax, P->wpb, st);
+            const int64_t tb = P->plain_first[p], te = P->plain_first[p + 1];
+            const unsigned grid = (unsigned)((te - tb + P->wpb - 1) / P->wpb);
+            cudaError_t e =
+                P->fwd_nl > 0 ? fwd_reg_launch(P->fwd_nl, a, tb, te, P->kmax, P->fwd_ld, grid,
+                                               P->wpb, 0, st)
+                : P->fwd_nl < 0
+                    ? fwd_reg_mixed_launch(a, tb, te, P->kmax, P->fwd_ld, grid, P->wpb, 0, st)
+                    : fwd_launch_plain(P->lmax, a, tb, te, P->kmax, P->wpb, st);
             if (e != cudaSuccess)
                 return fail(PQ_ERR_CUDA, "plain launch failed: %s", cudaGetErrorString(e));
         }
         return PQ_OK;
     }
     ExecArgs a = exec_args(P, src, amps, probs, true, partial);
+    if (P->fwd_nl != 0) {
+        cudaError_t e =
+            P->fwd_nl > 0 ? fwd_reg_launch(P->fwd_nl, a, 0, a.ntasks, P->kmax, P->fwd_ld,
+                                           (unsigned)P->blocks, P->wpb, 1, st)
+                          : fwd_reg_mixed_launch(a, 0, a.ntasks, P->kmax, P->fwd_ld,
+                                                 (unsigned)P->blocks, P->wpb, 1, st);
+        if (e != cudaSuccess)
+            return fail(PQ_ERR_CUDA, "persistent launch failed: %s", cudaGetErrorString(e));
+        return PQ_OK;
+    }
     cudaError_t e = fwd_launch_persistent(P->lmax, a, P->kmax, P->blocks, P->wpb, st);
     if (e != cudaSuccess)
         return fail(PQ_ERR_CUDA, "persistent launch failed: %s", cudaGetErrorString(e));
@@ -1632,6 +1692,8 @@ extern "C" int pq_autotune(pq_plan* P, const pq_batch* b, const pq_c128* U, void
         T->kind = P->kind;
         T->opts = P->opts;
         T->opts.method = PQ_METHOD_BATCHED;
+        // time the class with the walk the whole plan runs
+        T->opts.column_sums = P->fwd_nl == 0 ? PQ_SUMS_SHARED : PQ_SUMS_REGISTERS;
         T->opts.use_graph = 0;
         T->opts.chunk_log2 = 0;
         T->device = P->device;
@@ -1830,7 +1892,7 @@ int plan_run_forward(pq_plan* P, const void* src, void* amps, double* probs, cud
 
 int plan_prepare_forward(pq_plan* P)
 {
-    const cudaError_t e = fwd_prepare(P->lmax, P->wpb * fwd_smem_per_warp(P->kmax, P->lmax));
+    const cudaError_t e = forward_prepare(P);
     return e == cudaSuccess ? PQ_OK : fail(PQ_ERR_CUDA, "kernel attribute setup failed: %s",
                                             cudaGetErrorString(e));
 }

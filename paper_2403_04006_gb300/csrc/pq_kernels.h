@@ -63,6 +63,20 @@ cudaError_t fwd_launch_persistent(int lmax, const ExecArgs& a, int kmax, int blo
                                   cudaStream_t st);
 cudaError_t fwd_launch_plain(int lmax, const ExecArgs& a, int64_t t_begin, int64_t t_end,
                              int kmax, int wpb, cudaStream_t st);
+// The register-resident forward walk (glynn_fwd_reg_kernel<NL>) for product
+// sides of at most kFwdRegMaxLd columns: one instantiation per even column
+// bound NL = 4 .. 20 (fwd_reg_class_of(l)), launched per class.
+constexpr int kFwdRegMaxLd = 20;
+int fwd_reg_class_of(int l);
+int fwd_reg_smem_per_warp(int kmax, int ld);
+int fwd_reg_regs_per_thread(int nl);
+cudaError_t fwd_reg_prepare(int nl, int smem_bytes);
+cudaError_t fwd_reg_launch(int nl, const ExecArgs& a, int64_t t_begin, int64_t t_end, int kmax,
+                           int ld, unsigned grid, int wpb, int queue, cudaStream_t st);
+int fwd_reg_mixed_regs_per_thread();
+cudaError_t fwd_reg_mixed_prepare(int smem_bytes);
+cudaError_t fwd_reg_mixed_launch(const ExecArgs& a, int64_t t_begin, int64_t t_end, int kmax,
+                                 int ld, unsigned grid, int wpb, int queue, cudaStream_t st);
 
 // ---- backward (glynn_bwd.cu)
 struct BwdArgs {

@@ -82,6 +82,15 @@ struct pq_plan {
     int32_t* err_d = nullptr;
     // backward schedule and workspace (built on the first backward call)
     bool bwd_ready = false;
+    // where the forward walk keeps its column sums: 0 shared memory; NL > 0
+    // registers, every permanent in column class NL (glynn_fwd_reg_kernel<NL>);
+    // -1 registers, several classes (glynn_fwd_reg_mixed_kernel)
+    int fwd_nl = 0;
+    // columns of a row of the forward walk's shared-memory layout: lmax for
+    // shared memory; the class bound of the widest permanent for registers
+    // (a row of class NL holds NL columns, at least 4, so it can be wider
+    // than lmax)
+    int fwd_ld = 0;
     bool uploaded = false;  // device data matches the host schedule (a failed re-plan clears it)
     std::vector<pqi::PermDesc> desc_bwd_h;
     std::vector<pqi::Task> tasks_bwd_plain_h, tasks_bwd_batched_h;

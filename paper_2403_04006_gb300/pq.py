@@ -26,6 +26,7 @@ PQ_ERR_NOMEM = -5
 PQ_ERR_STATE = -6
 PQ_METHOD_BATCHED = 0
 PQ_METHOD_PLAIN = 1
+PQ_SUMS_AUTO, PQ_SUMS_SHARED, PQ_SUMS_REGISTERS = 0, 1, 2
 PQ_MAX_N = 48
 PQ_DEVERR_TASK_PERM = 1
 PQ_DEVERR_TASK_PART = 2
@@ -51,14 +52,14 @@ class pq_batch_sizes(ctypes.Structure):
 class pq_plan_options(ctypes.Structure):
     _fields_ = [("method", _i32), ("use_graph", _i32), ("chunk_log2", _i32),
                 ("warps_per_block", _i32), ("blocks_per_sm", _i32), ("shard_index", _i32),
-                ("shard_count", _i32), ("reserved", _i32)]
+                ("shard_count", _i32), ("column_sums", _i32)]
 
 
 class pq_plan_stats(ctypes.Structure):
     _fields_ = [("permanents", _i64), ("terms", _i64), ("flops_forward", ctypes.c_double),
                 ("flops_backward", ctypes.c_double), ("tasks", _i64),
                 ("launches_forward", _i64), ("launches_backward", _i64), ("lmax", _i32),
-                ("reserved", _i32), ("fp64_instr_forward", ctypes.c_double),
+                ("column_sums", _i32), ("fp64_instr_forward", ctypes.c_double),
                 ("fp64_instr_backward", ctypes.c_double),
                 ("fp64_instr_forward_executed", ctypes.c_double)]
 

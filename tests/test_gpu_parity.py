@@ -452,6 +452,69 @@ def test_backward_every_product_width(dev):
         assert pq.pq_plan_device_error(plan.handle) == (0, 0)
 
 
+def walk_items(rng):
+    """Product widths 1 .. 20 in one batch: random ragged items with repeated
+    rows and columns (n <= 14), the width items of the backward test and
+    all-distinct permanents of widths 17 .. 20."""
+    items = random_items(80, 1, 14, rng) + width_items(rng)
+    A = W.single_large(30)
+    for l in range(17, 21):
+        items.append((A[:l, :l], [1] * l, [1] * l))
+    return items
+
+
+@pytest.mark.parametrize("method", ["batched", "plain"])
+def test_register_and_shared_walks_agree(dev, method):
+    """The forward walk with column sums in registers (one instantiation per
+    class of product widths; a batch mixing classes runs them all in one
+    launch) and in shared memory: with the same chunks the same bits, and
+    the oracle's permanents; a batch of one width class takes registers by
+    default, a mixed one shared memory."""
+    rng = np.random.default_rng(410)
+    items = walk_items(rng)
+    pb = W.pack_batch(items)
+    db = api.DeviceBatch(pb, dev)
+    outs = {}
+    for cs in ("shared", "registers"):
+        plan = api.Plan.for_batch(pb, method=method, chunk_log2=6, column_sums=cs)
+        assert plan.stats()["column_sums"] == cs
+        outs[cs] = api.permanent_batched(db, plan).cpu().numpy()
+        assert pq.pq_plan_device_error(plan.handle) == (0, 0)
+    assert np.array_equal(outs["shared"].view(np.float64), outs["registers"].view(np.float64))
+    ref = oracle_items(items)
+    assert rel_err(outs["registers"], ref).max() <= TOL
+    assert api.Plan.for_batch(pb).stats()["column_sums"] == "shared"
+    w = product_columns(pb)
+    idx = np.nonzero((w == 11) | (w == 12))[0]
+    assert idx.size >= 2
+    assert api.Plan.for_batch(pb.subset(idx)).stats()["column_sums"] == "registers"
+
+
+@pytest.mark.parametrize("method", ["batched", "plain"])
+def test_register_walk_of_one_class_narrower_than_its_bound(dev, method):
+    """Batches of one column class whose widest permanent is narrower than
+    the class's register count (at most 3 product columns: 4 registers; 5: 6;
+    11: 12), run by default with the column sums in registers: the oracle's
+    and the shared-memory walk's permanents, no device error."""
+    rng = np.random.default_rng(411)
+    items = walk_items(rng)
+    pb = W.pack_batch(items)
+    w = product_columns(pb)
+    ref_all = oracle_items(items)
+    for sel in (w <= 3, w == 5, w == 11):
+        idx = np.nonzero(sel)[0]
+        assert idx.size >= 1
+        sub = pb.subset(idx)
+        db = api.DeviceBatch(sub, dev)
+        plan = api.Plan.for_batch(sub, method=method)
+        assert plan.stats()["column_sums"] == "registers"
+        got = api.permanent_batched(db, plan).cpu().numpy()
+        assert pq.pq_plan_device_error(plan.handle) == (0, 0)
+        assert rel_err(got, ref_all[idx]).max() <= TOL
+        shared = api.Plan.for_batch(sub, method=method, column_sums="shared")
+        assert rel_err(got, api.permanent_batched(db, shared).cpu().numpy()).max() <= TOL
+
+
 def test_permanent_gradcheck(dev):
     rng = np.random.default_rng(505)
     items = random_items(4, 2, 5, rng)
