@@ -532,9 +532,11 @@ int pq_debug_corrupt_plan(pq_plan* plan, int32_t what);
 
 /* ---- Diagnostics (host only; no GPU needed) ---------------------------- */
 
-/* How the planner treats one permanent: the side it sums, the digits of the
- * mixed-radix Gray code (ascending radix; digit d belongs to summed row
- * row_of_digit[d]) and how the code is cut into chunks. */
+/* How the planner treats one permanent in a batched forward plan: the side it
+ * sums, the digits of the mixed-radix Gray code (digit d belongs to summed
+ * row row_of_digit[d]; the J low digits walked inside a chunk come first, then
+ * the others, each group in ascending radix) and how the code is cut into
+ * chunks. */
 typedef struct {
     int32_t n, k, l;     /* photons; summed rows and product columns after orientation */
     int32_t transposed;  /* 1 if the input's columns became the summed side         */

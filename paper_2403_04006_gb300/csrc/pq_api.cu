@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <numeric>
 #include <queue>
@@ -211,10 +212,73 @@ static double weight_change_rate(const std::vector<int32_t>& drad, int j)
     return a == j ? 0.0 : std::ldexp(1.0, -a);
 }
 
+// Put the digits of the given low multiset first (ascending radix, ties in
+// row order), then the others in the same order.  low_count[v]: how many
+// digits of radix v go low.  The walk takes any digits as its low ones: the
+// Gray code over all digits is the same set of codes in another order.
+static void order_digits(ItemPlan& it, const std::vector<int>& low_count)
+{
+    const int nd = (int)it.drad.size();
+    std::vector<int> idx(nd), taken(low_count.size(), 0), lo, hi;
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        return it.drad[a] != it.drad[b] ? it.drad[a] < it.drad[b] : it.drow[a] < it.drow[b];
+    });
+    for (int d : idx) {
+        const int v = it.drad[d];
+        if (v < (int)low_count.size() && taken[v] < low_count[v]) {
+            ++taken[v];
+            lo.push_back(d);
+        } else {
+            hi.push_back(d);
+        }
+    }
+    lo.insert(lo.end(), hi.begin(), hi.end());
+    std::vector<int32_t> r(nd), rad(nd), top(nd);
+    for (int q = 0; q < nd; ++q) {
+        r[q] = it.drow[lo[q]];
+        rad[q] = it.drad[lo[q]];
+        top[q] = it.dtop[lo[q]];
+    }
+    it.drow = r;
+    it.drad = rad;
+    it.dtop = top;
+}
+
+// FP64 warp instructions of a cut, the quantity the batched cut minimises:
+// per task, L terms of per_term (plus per_weight times the rate at which the
+// low-digit weight changes), per_high per high digit for the chunk start,
+// per_task_low per low digit and per_task once.
+struct CutCost {
+    double per_term = 0.0, per_weight = 0.0, per_high = 0.0, per_task = 0.0, per_task_low = 0.0;
+};
+
+// The forward kernel's costs: Gray step 2l, the products 4 each, the fused
+// accumulation 4, the double-double fold 10 every 32 terms; 2 DFMA per weight
+// change; a chunk start 2l + 2 per high digit; 84 per lane for the chunk's
+// fold, weight and lane tree, and the staging (2k).
+static CutCost forward_cut_cost(const ItemPlan& it)
+{
+    int cmax = 1;
+    for (int c : it.cmul)
+        cmax = std::max(cmax, c);
+    const double products = (cmax == 1) ? (it.l - 2) : (it.l + cmax - 3);
+    CutCost cc;
+    cc.per_term = 2.0 * it.l + 4.0 * std::max(products, 0.0) + 4.0 + 10.0 / 32.0;
+    cc.per_weight = 2.0;
+    cc.per_high = 2.0 * it.l + 2.0;
+    cc.per_task = 84.0 + 2.0 * it.k;
+    return cc;
+}
+
 // Cut the item's code into chunks of the lowest digits: the longest prefix of
-// digits whose radix product stays within the target length.
+// digits whose radix product stays within the target length.  With reorder
+// (batched plans), the low digits may be any sub-multiset of the digits, not
+// only a prefix of the ascending list; see below.  cc: the kernel's costs
+// (default: the forward's).
 static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
-                          int64_t min_chunks = kWarp)
+                          int64_t min_chunks = kWarp, bool reorder = false,
+                          const CutCost* cc = nullptr)
 {
     if (it.trivial) {
         it.J = 0;
@@ -222,6 +286,8 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
         it.nchunks = 0;
         return;
     }
+    if (reorder)  // start from the ascending order, whatever an earlier cut chose
+        order_digits(it, {});
     int64_t target = it.T / min_chunks;  // aim for at least min_chunks chunks
     int64_t cap = int64_t(1) << std::max(0, std::min(log2_cap, 30));
     if (target > cap)
@@ -240,17 +306,16 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
         // to two shorter) take the one with the fewest FP64 warp instructions:
         // every lane of a task executes L terms whether or not it has a chunk,
         // and every task pays its chunk start-up and reductions.
-        int cmax = 1;
-        for (int c : it.cmul)
-            cmax = std::max(cmax, c);
+        const CutCost k = cc ? *cc : forward_cut_cost(it);
         const int nd = (int)it.drad.size();
-        auto cost_of = [&](int j, int64_t lj) {
-            const double products = (cmax == 1) ? (it.l - 2) : (it.l + cmax - 3);
-            const double ppt = 2.0 * it.l + 4.0 * std::max(products, 0.0) + 4.0 +
-                               2.0 * weight_change_rate(it.drad, j) + 10.0 / 32.0;
-            const double ovh = (nd - j) * (2.0 * it.l + 2.0) + 84.0 + 2.0 * it.k;
+        auto cost_rate = [&](int j, int64_t lj, double wrate) {
+            const double ppt = k.per_term + k.per_weight * wrate;
+            const double ovh = (nd - j) * k.per_high + k.per_task + j * k.per_task_low;
             const int64_t tasks = (it.T / lj + kWarp - 1) / kWarp;
             return tasks * ((double)lj * ppt + ovh);
+        };
+        auto cost_of = [&](int j, int64_t lj) {
+            return cost_rate(j, lj, weight_change_rate(it.drad, j));
         };
         int bestJ = J;
         int64_t bestL = L;
@@ -273,6 +338,68 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
         }
         J = bestJ;
         L = bestL;
+        if (reorder) {
+            // Any sub-multiset of the digits can be the low ones.  The number
+            // of chunks is the product of the high radices, and a task is 32
+            // of them, so the prefix cuts often leave most lanes of a
+            // permanent's last task without a chunk (36 chunks: two tasks, 28
+            // idle lanes); choosing which radices go low finds chunk counts
+            // that fill the tasks (ragged batch: 3.9% fewer FP64 instructions
+            // by this model).  Depth-first over the counts of each distinct
+            // radix, products within the cap, at most 4096 cuts evaluated;
+            // a cut replaces the prefix cut only if 0.1% cheaper.
+            std::vector<int> vals, cnt;
+            for (int v : it.drad) {
+                if (v > kMaxLowRadix)
+                    break;  // ascending: no larger radix can go low
+                if (vals.empty() || vals.back() != v) {
+                    vals.push_back(v);
+                    cnt.push_back(0);
+                }
+                ++cnt.back();
+            }
+            std::vector<int> cur(vals.size(), 0), bestc;
+            int budget = 4096;
+            std::function<void(size_t, int, int64_t)> dfs = [&](size_t i, int j, int64_t lj) {
+                if (budget <= 0)
+                    return;
+                if (i == vals.size()) {
+                    --budget;
+                    const int a2 = (!vals.empty() && vals[0] == 2) ? cur[0] : 0;
+                    const double wr = (a2 == j) ? 0.0 : std::ldexp(1.0, -a2);
+                    const double c = cost_rate(j, lj, wr);
+                    if (c < best * 0.999) {
+                        best = c;
+                        bestc = cur;
+                    }
+                    return;
+                }
+                int64_t p = lj;
+                for (int a = 0; a <= cnt[i] && j + a <= jmax; ++a) {
+                    if (a > 0) {
+                        if (p > cap / vals[i])
+                            break;
+                        p *= vals[i];
+                    }
+                    cur[i] = a;
+                    dfs(i + 1, j + a, p);
+                }
+                cur[i] = 0;
+            };
+            dfs(0, 0, 1);
+            if (!bestc.empty()) {
+                std::vector<int> low_count(kMaxLowRadix + 1, 0);
+                J = 0;
+                L = 1;
+                for (size_t i = 0; i < vals.size(); ++i) {
+                    low_count[vals[i]] = bestc[i];
+                    J += bestc[i];
+                    for (int a = 0; a < bestc[i]; ++a)
+                        L *= vals[i];
+                }
+                order_digits(it, low_count);
+            }
+        }
     }
     it.J = J;
     it.L = L;
@@ -388,10 +515,12 @@ static void free_plan_device(pq_plan* P)
                     P->item_k_d,      P->item_l_d,         P->grad_out_tmp_d, P->bs_pos_d};
     for (void* p : ptrs)
         dev_free(p);
-    void* bptrs[] = {P->desc_bwd_d, P->tasks_bwd_plain_d, P->tasks_bwd_batched_d};
+    void* bptrs[] = {P->desc_bwd_d, P->tasks_bwd_plain_d, P->tasks_bwd_batched_d,
+                     P->meta_bwd_d};
     for (void* p : bptrs)
         dev_free(p);
     P->desc_bwd_d = nullptr;
+    P->meta_bwd_d = nullptr;
     P->tasks_bwd_plain_d = P->tasks_bwd_batched_d = nullptr;
     P->bwd_ready = false;
     P->desc_d = nullptr;
@@ -513,7 +642,7 @@ static int schedule_and_upload(pq_plan* P)
             double total = 0.0, longest = 0.0;
             for (ItemPlan& it : P->items) {
                 const int e = explicit_log2_for(P, it);
-                choose_chunks(it, e > 0 ? e : std::min(10, gcap), kMaxLowDigits, kWarp);
+                choose_chunks(it, e > 0 ? e : std::min(10, gcap), kMaxLowDigits, kWarp, true);
                 if (it.trivial)
                     continue;
                 const double cost = (double)it.L * fwd_flops_per_term(it) +
@@ -1295,10 +1424,35 @@ static int ensure_backward(pq_plan* P)
     std::vector<int64_t> gpart_off(np), gl_off(np);
     int64_t gpart = 0, gl = 0;
     double instr_b = 0.0;
+    // The backward cuts each permanent with its own costs and its own choice
+    // of low digits (any sub-multiset, as the forward), so its digit order
+    // can differ from the forward's: the backward reads a copy of the
+    // metadata pool whose digit sections follow its order.
+    std::vector<int32_t> meta_bwd = P->meta_h;
     for (int64_t p = 0; p < np; ++p) {
         ItemPlan& it = items[p];
         const BwdClass& C = cls[P->bwd_class_of[p]];
-        choose_chunks(it, kBwdChunkLog2, std::max(C.jb, 1));
+        if (!it.trivial) {
+            // per term as glynn_bwd.cu counts it; a chunk start 2l per high
+            // digit; per task the staging (k), the lane contraction (2l per
+            // low digit, about 2kl) and the gradient write
+            CutCost bc;
+            bc.per_term = bwd_instr_per_term(it, C.reg != 0);
+            bc.per_high = 2.0 * it.l;
+            bc.per_task = it.k + 66.0 * it.k * it.l / 32.0;
+            bc.per_task_low = 2.0 * it.l;
+            choose_chunks(it, kBwdChunkLog2, std::max(C.jb, 1), kWarp, true, &bc);
+            const PermDesc& Df = P->desc_h[p];
+            const int nd = (int)it.drow.size();
+            int32_t* dig = meta_bwd.data() + Df.meta + 2 * Df.k + 2 * Df.l;
+            for (int d = 0; d < nd; ++d) {
+                dig[d] = it.drow[d];
+                dig[nd + d] = it.drad[d];
+                dig[2 * nd + d] = it.dtop[d];
+            }
+        } else {
+            choose_chunks(it, kBwdChunkLog2, std::max(C.jb, 1));
+        }
         PermDesc& D = P->desc_bwd_h[p];
         D.J = it.J;
         D.L = it.L;
@@ -1366,6 +1520,8 @@ static int ensure_backward(pq_plan* P)
 
     int rc;
     if ((rc = dev_upload(&P->desc_bwd_d, P->desc_bwd_h)) != PQ_OK)
+        return rc;
+    if ((rc = dev_upload(&P->meta_bwd_d, meta_bwd)) != PQ_OK)
         return rc;
     if ((rc = dev_upload(&P->tasks_bwd_plain_d, P->tasks_bwd_plain_h)) != PQ_OK)
         return rc;
@@ -1449,7 +1605,7 @@ static int run_backward(pq_plan* P, const void* src, const pq_c128* grad_out, co
         return PQ_OK;
     BwdArgs a;
     a.desc = P->desc_bwd_d;
-    a.meta = P->meta_d;
+    a.meta = P->meta_bwd_d;
     a.ntasks = (int64_t)P->tasks_bwd_plain_h.size();
     a.src = reinterpret_cast<const double2*>(src);
     a.grad_out = reinterpret_cast<const double2*>(grad_out);
@@ -1519,7 +1675,7 @@ extern "C" int pq_permanent_backward(const pq_batch* b, const pq_c128* grad_out,
     }
     int rc = run_backward(P, b->mats, grad_out, nullptr, nullptr, st);
     if (rc == PQ_OK && P->nperm > 0) {
-        cudaError_t e = scatter_grad_batch(P->desc_bwd_d, P->meta_d, P->nperm, P->grad_local_d,
+        cudaError_t e = scatter_grad_batch(P->desc_bwd_d, P->meta_bwd_d, P->nperm, P->grad_local_d,
                                            P->grad_local_off_d, P->item_mat_off_d, P->item_l_d,
                                            P->item_k_d, reinterpret_cast<double2*>(grad_mats),
                                            P->total_mat_elems, st);
@@ -1773,7 +1929,7 @@ extern "C" int pq_plan_item_info(int32_t k, int32_t l, const int32_t* row_mult,
     int rc = build_item(row_mult, col_mult, k, l, 0, l, it);
     if (rc != PQ_OK)
         return rc;
-    choose_chunks(it, chunk_log2 > 0 ? chunk_log2 : 10);
+    choose_chunks(it, chunk_log2 > 0 ? chunk_log2 : 10, kMaxLowDigits, kWarp, true);
     std::memset(out, 0, sizeof(*out));
     out->n = it.n;
     out->k = it.k;

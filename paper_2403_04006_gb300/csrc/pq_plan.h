@@ -75,6 +75,7 @@ struct pq_plan {
     // device
     pqi::PermDesc* desc_d = nullptr;
     int32_t* meta_d = nullptr;
+    int32_t* meta_bwd_d = nullptr;  // the metadata pool with the backward's digit order
     pqi::Task* tasks_batched_d = nullptr;
     pqi::Task* tasks_plain_d = nullptr;
     double* partials_d = nullptr;

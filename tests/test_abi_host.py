@@ -94,7 +94,8 @@ def test_planner_side_choice_and_term_count(lib, r, c):
     assert info.terms == min(Tr, Tc)
     assert info.transposed == (1 if Tc < Tr else 0)
     rad = list(info.radix[:info.ndig])
-    assert rad == sorted(rad)
+    # the chunk's (low) digits first, then the others, each in ascending radix
+    assert rad[:info.J] == sorted(rad[:info.J]) and rad[info.J:] == sorted(rad[info.J:])
     assert math.prod(rad) == info.terms
     assert info.chunk_len == math.prod(rad[:info.J])
     assert info.chunks * info.chunk_len == info.terms
@@ -178,3 +179,4 @@ def test_loop_poly_factors_reproduce_the_polynomial(lib, N):
         if N % 2:
             h *= l
         assert abs(h - direct) <= 1e-13 * scale, (N, h, direct)
+
