@@ -62,6 +62,7 @@ WORKLOAD = ("ragged batch: 65536 permanents, n ~ U{4..20}, row/col multiplicitie
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, NVIDIA's figure
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "glynn_fwd_persistent_ragged65536.md")
 KERNEL_SOURCES = ["paper_2403_04006_gb300/csrc/glynn_fwd.cu",
+                  "paper_2403_04006_gb300/csrc/pq_fixsum.cuh",
                   "paper_2403_04006_gb300/csrc/pq_device.cuh",
                   "paper_2403_04006_gb300/csrc/pq_internal.h"]
 

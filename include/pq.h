@@ -554,6 +554,14 @@ typedef struct {
 int pq_plan_item_info(int32_t k, int32_t l, const int32_t* row_mult, const int32_t* col_mult,
                       int32_t chunk_log2, pq_item_info* out);
 
+/* The exact warp sum of the forward kernels' lane reduction, run on the host:
+ * out[0] + out[1] = sum_q (hi[q] + lo[q]) over n <= 32 finite pairs (host
+ * arrays), exact except for bits below 2^-64 of the last significand bit of
+ * the largest input, truncated; out[0] holds the leading 53 bits, out[1] the
+ * leading 53 bits of the rest.  PQ_ERR_ARG: n outside [0, 32], a null
+ * pointer or a value that is not finite. */
+int pq_fixsum_host(const double* hi, const double* lo, int32_t n, double* out);
+
 /* Run the kernels' warp-uniform Gray walk on the host: ndig <= 15 digits with
  * radix[d] in [2, 15]; for `steps` steps writes the digit that changes and
  * its direction (+1 / -1) to host arrays digit[steps], dir[steps]. */

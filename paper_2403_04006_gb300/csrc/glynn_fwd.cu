@@ -24,12 +24,14 @@
 //     radix > 2 scale one factor (two DMUL);
 //   * every 16 terms the FP64 running sum is folded into a double-double
 //     accumulator with TwoSum.
-// A warp task is up to 32 chunks of one permanent (one per lane).  Lanes are
-// reduced in a fixed tree order and the tasks of one permanent in task order
-// by the warp that finishes last, so results do not depend on scheduling.
+// A warp task is up to 32 chunks of one permanent (one per lane).  The lanes'
+// sums are added exactly, in 128-bit integers (pq_fixsum.cuh), and the tasks
+// of one permanent in task order by the warp that finishes last, so results
+// do not depend on scheduling.
 #include <cuda_runtime.h>
 
 #include "pq_device.cuh"
+#include "pq_fixsum.cuh"
 #include "pq_kernels.h"
 
 namespace pqi {
@@ -198,6 +200,37 @@ __device__ __forceinline__ void finalize(const ExecArgs& a, const PermDesc& D, d
 
 __device__ void combine_task(const ExecArgs& a, const Task& t, const PermDesc& D, dd2 res, int lane);
 
+// The task's sum: every lane's chunk sum (rh + rl, ih + il) times its
+// high-digit weight (-1)^neg whigh_u (zero for a lane without a chunk), added
+// over the warp exactly in integer arithmetic (pq_fixsum.cuh); every lane gets
+// it.  When no lane's weight is above 1 the weight is a sign, applied to the
+// bit patterns, and the double-double product (14 FP64 operations) is skipped.
+__device__ __forceinline__ dd2 task_sum(double rh, double rl, double ih, double il,
+                                        uint64_t whigh_u, bool neg, bool active)
+{
+    if (__any_sync(0xffffffffu, active && whigh_u != 1)) {
+        double w = active ? (double)whigh_u : 0.0;
+        if (neg)
+            w = -w;
+        fast_two_sum(rh, rl, rh, rl);
+        fast_two_sum(ih, il, ih, il);
+        dd_mul_d(rh, rl, w);
+        dd_mul_d(ih, il, w);
+    } else if (!active) {
+        rh = rl = ih = il = 0.0;
+    } else if (neg) {
+        const uint64_t s = 1ull << 63;
+        rh = fix_double(fix_bits(rh) ^ s);
+        rl = fix_double(fix_bits(rl) ^ s);
+        ih = fix_double(fix_bits(ih) ^ s);
+        il = fix_double(fix_bits(il) ^ s);
+    }
+    dd2 res;
+    warp_fix_sum(rh, rl, res.rh, res.rl);
+    warp_fix_sum(ih, il, res.ih, res.il);
+    return res;
+}
+
 __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int& staged, int lane)
 {
     const PermDesc D = a.desc[t.perm];
@@ -241,9 +274,6 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
             whigh_u *= binom_u64(mv.dtop[d], g);
             gpar += g;
         }
-        double whigh = active ? (double)whigh_u : 0.0;
-        if (gpar & 1)
-            whigh = -whigh;
 
         // ---- warp-uniform walk over the low digits
         LowWalk wk;
@@ -300,15 +330,7 @@ __device__ void process_task(const ExecArgs& a, const Task& t, WarpSmem& sm, int
         }
         dd_acc(rh, rl, acc.x);
         dd_acc(ih, il, acc.y);
-        fast_two_sum(rh, rl, rh, rl);
-        fast_two_sum(ih, il, ih, il);
-        dd_mul_d(rh, rl, whigh);
-        dd_mul_d(ih, il, whigh);
-        res.rh = rh;
-        res.rl = rl;
-        res.ih = ih;
-        res.il = il;
-        res = warp_sum_dd2(res);
+        res = task_sum(rh, rl, ih, il, whigh_u, (gpar & 1) != 0, active);
     }
     combine_task(a, t, D, res, lane);
 }
@@ -344,7 +366,8 @@ __device__ void combine_task(const ExecArgs& a, const Task& t, const PermDesc& D
         dd_add(tot.rh, tot.rl, __ldcg(pp + 0), __ldcg(pp + 1));
         dd_add(tot.ih, tot.il, __ldcg(pp + 2), __ldcg(pp + 3));
     }
-    tot = warp_sum_dd2(tot);
+    warp_fix_sum(tot.rh, tot.rl, tot.rh, tot.rl);
+    warp_fix_sum(tot.ih, tot.il, tot.ih, tot.il);
     if (lane == 0)
         finalize(a, D, tot);
 }
@@ -486,8 +509,8 @@ __device__ __forceinline__ bool reg_step(LowWalk& wk, const RegSmem& sm, double2
     return ((wk.radm1 >> (4 * d)) & 15u) > 1u;
 }
 
-// The walk of this lane's chunk c (as in process_task); returns the lane's
-// double-double sum times its high-digit weight, before the lane reduction.
+// The walk of this lane's chunk c (as in process_task); returns the task's
+// sum over the warp (task_sum).
 template <int NL>
 __device__ __forceinline__ dd2 reg_walk(const PermDesc& D, const MetaView& mv, const RegSmem& sm,
                                         int64_t c, bool active)
@@ -514,9 +537,6 @@ __device__ __forceinline__ dd2 reg_walk(const PermDesc& D, const MetaView& mv, c
         whigh_u *= binom_u64(mv.dtop[d], g);
         gpar += g;
     }
-    double whigh = active ? (double)whigh_u : 0.0;
-    if (gpar & 1)
-        whigh = -whigh;
 
     LowWalk wk;
     wk.v = 0;
@@ -565,16 +585,7 @@ __device__ __forceinline__ dd2 reg_walk(const PermDesc& D, const MetaView& mv, c
     }
     dd_acc(rh, rl, acc.x);
     dd_acc(ih, il, acc.y);
-    fast_two_sum(rh, rl, rh, rl);
-    fast_two_sum(ih, il, ih, il);
-    dd_mul_d(rh, rl, whigh);
-    dd_mul_d(ih, il, whigh);
-    dd2 res;
-    res.rh = rh;
-    res.rl = rl;
-    res.ih = ih;
-    res.il = il;
-    return res;
+    return task_sum(rh, rl, ih, il, whigh_u, (gpar & 1) != 0, active);
 }
 
 template <int NL>
@@ -593,7 +604,6 @@ __device__ void process_task_reg(const ExecArgs& a, const Task& t, RegSmem& sm, 
         const int64_t chunk0 = (int64_t)t.part * kWarp;
         const bool active = chunk0 + lane < D.nchunks;
         res = reg_walk<NL>(D, mv, sm, active ? (chunk0 + lane) : 0, active);
-        res = warp_sum_dd2(res);
     }
     combine_task(a, t, D, res, lane);
 }
@@ -666,7 +676,7 @@ __device__ __forceinline__ void run_task(const ExecArgs& a, int64_t ti, WarpSmem
 // the global counter until the range is exhausted (persistent launch of a
 // whole batch); queue == 0: warp w of block b takes task t_begin + b * wpb + w
 // (one launch per permanent, the plain method).
-__global__ void __launch_bounds__(256) glynn_fwd_kernel(ExecArgs a, int64_t t_begin,
+__global__ void __launch_bounds__(256, 2) glynn_fwd_kernel(ExecArgs a, int64_t t_begin,
                                                          int64_t t_end, int kmax, int ld,
                                                          int queue)
 {

@@ -1,6 +1,10 @@
 // pq_diag.cu -- host-side runs of device helpers, for tests without a GPU.
+#include <algorithm>
+#include <cmath>
+
 #include "../../include/pq.h"
 #include "pq_device.cuh"
+#include "pq_fixsum.cuh"
 
 extern "C" int pq_gray_walk(const int32_t* radix, int32_t ndig, int64_t steps, int32_t* digit,
                             int32_t* dir)
@@ -28,5 +32,32 @@ extern "C" int pq_gray_walk(const int32_t* radix, int32_t ndig, int64_t steps, i
         digit[s] = pqi::low_step(w, up);
         dir[s] = up;
     }
+    return PQ_OK;
+}
+
+// The forward kernels' exact warp sum, run on the host: the same conversion,
+// the same 26-bit limbs added as 32-bit words (as redux.sync adds them) and
+// the same conversion back, over n <= 32 lanes.
+extern "C" int pq_fixsum_host(const double* hi, const double* lo, int32_t n, double* out)
+{
+    if (n < 0 || n > 32 || !out || (n > 0 && (!hi || !lo)))
+        return PQ_ERR_ARG;
+    int emax = 1;
+    for (int q = 0; q < n; ++q) {
+        if (!std::isfinite(hi[q]) || !std::isfinite(lo[q]))
+            return PQ_ERR_ARG;
+        emax = std::max(emax, std::max(pqi::fix_exp(hi[q]), pqi::fix_exp(lo[q])));
+    }
+    uint32_t sum[4] = {0, 0, 0, 0};
+    int32_t top = 0;
+    for (int q = 0; q < n; ++q) {
+        uint32_t limb[4];
+        int32_t t;
+        pqi::fix_limbs(pqi::fix_of(hi[q], emax) + pqi::fix_of(lo[q], emax), limb, t);
+        for (int w = 0; w < 4; ++w)
+            sum[w] += limb[w];
+        top += t;
+    }
+    pqi::fix_to_dd(pqi::fix_from_limbs(sum, top), emax, out[0], out[1]);
     return PQ_OK;
 }

@@ -8,6 +8,7 @@ import itertools
 import math
 import os
 import re
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -180,3 +181,73 @@ def test_loop_poly_factors_reproduce_the_polynomial(lib, N):
             h *= l
         assert abs(h - direct) <= 1e-13 * scale, (N, h, direct)
 
+
+def fixsum(lib, hi, lo):
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    out = np.zeros(2)
+    rc = lib.pq_fixsum_host(hi.ctypes.data_as(ctypes.c_void_p), lo.ctypes.data_as(ctypes.c_void_p),
+                            len(hi), out.ctypes.data_as(ctypes.c_void_p))
+    return rc, out
+
+
+def _trunc53(x):
+    """Leading 53 bits of the rational x, truncated towards zero, as a double."""
+    if x == 0:
+        return 0.0
+    s = -1 if x < 0 else 1
+    a = abs(x)
+    e = math.floor(math.log2(a.numerator) - math.log2(a.denominator))
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    ulp = Fraction(2) ** (e - 52)
+    return s * float(math.floor(a / ulp) * ulp)
+
+
+@pytest.mark.parametrize("case", ["random", "cancel", "spread", "tiny", "signs"])
+def test_exact_warp_sum_is_the_truncated_exact_sum(lib, case):
+    """The forward kernels' lane reduction adds 32 double-double lane sums in
+    128-bit integers: out[0] must be the exact sum's leading 53 bits and
+    out[1] the rest's, for inputs whose bits all lie within 2^-64 of the
+    largest value's last bit (then nothing is dropped); zeros, cancellation,
+    subnormal-free spreads of exponent and mixed signs."""
+    rng = np.random.default_rng({"random": 1, "cancel": 2, "spread": 3, "tiny": 4, "signs": 5}[case])
+    n = 32
+    hi = rng.standard_normal(n) * 2.0 ** rng.integers(-8, 8, n)
+    if case == "cancel":
+        hi[16:] = -hi[:16] * (1 + 2.0 ** -50)
+    if case == "spread":
+        hi = hi * 2.0 ** rng.integers(-10, 0, n)
+    if case == "tiny":
+        hi = hi * 1e-280
+    if case == "signs":
+        hi[::3] = 0.0
+    lo = np.array([h * 2.0 ** -53 * u for h, u in zip(hi, rng.uniform(-1, 1, n))])
+    # keep every bit within 2^-64 of the largest value's last significand bit
+    unit = 2.0 ** (math.frexp(float(np.abs(hi).max()))[1] - 1 - 52 - 64)
+    lo = np.round(lo / unit) * unit
+    rc, out = fixsum(lib, hi, lo)
+    assert rc == 0
+    exact = sum((Fraction(float(h)) + Fraction(float(l)) for h, l in zip(hi, lo)), Fraction(0))
+    assert out[0] == _trunc53(exact)
+    assert out[1] == _trunc53(exact - Fraction(float(out[0])))
+
+
+def test_exact_warp_sum_drops_only_bits_far_below_the_largest(lib):
+    """A value more than 64 bits below the largest one's last bit is dropped
+    (truncated), an error below 2^-116 relative to the largest; lane counts 0
+    and 1; bad arguments."""
+    hi = np.array([1.0, 2.0 ** -120, -(2.0 ** -125)])
+    lo = np.array([2.0 ** -60, 0.0, 0.0])
+    rc, out = fixsum(lib, hi, lo)
+    assert rc == 0
+    exact = Fraction(1) + Fraction(2) ** -60
+    assert Fraction(float(out[0])) + Fraction(float(out[1])) == exact
+    rc, out = fixsum(lib, [], [])
+    assert rc == 0 and out[0] == 0.0 and out[1] == 0.0
+    rc, out = fixsum(lib, [-3.5], [2.0 ** -60])
+    assert rc == 0 and Fraction(float(out[0])) + Fraction(float(out[1])) == Fraction(-7, 2) + Fraction(2) ** -60
+    assert fixsum(lib, [np.inf], [0.0])[0] == pq.PQ_ERR_ARG
+    assert fixsum(lib, np.ones(33), np.zeros(33))[0] == pq.PQ_ERR_ARG
