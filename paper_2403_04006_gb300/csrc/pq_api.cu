@@ -248,15 +248,21 @@ static void order_digits(ItemPlan& it, const std::vector<int>& low_count)
 // FP64 warp instructions of a cut, the quantity the batched cut minimises:
 // per task, L terms of per_term (plus per_weight times the rate at which the
 // low-digit weight changes), per_high per high digit for the chunk start,
-// per_task_low per low digit and per_task once.
+// per_task_low per low digit and per_task once; per_task_weighted more when
+// the low-digit weight is not constant (a low radix above 2) and
+// per_task_whigh more when a high digit can carry a weight above 1 (a high
+// radix above 2).
 struct CutCost {
     double per_term = 0.0, per_weight = 0.0, per_high = 0.0, per_task = 0.0, per_task_low = 0.0;
+    double per_task_weighted = 0.0, per_task_whigh = 0.0;
 };
 
 // The forward kernel's costs: Gray step 2l, the products 4 each, the fused
 // accumulation 4, the double-double fold 10 every 32 terms; 2 DFMA per weight
-// change; a chunk start 2l + 2 per high digit; 84 per lane for the chunk's
-// fold, weight and lane tree, and the staging (2k).
+// change; a chunk start 2l + 2 per high digit; per lane and task the chunk's
+// last fold (8), the weighted run's (4), the high-digit weight's double-double
+// product (14, when some high digit has radix > 2; the lane sum itself is
+// integer work) and the staging (2k).
 static CutCost forward_cut_cost(const ItemPlan& it)
 {
     int cmax = 1;
@@ -267,7 +273,9 @@ static CutCost forward_cut_cost(const ItemPlan& it)
     cc.per_term = 2.0 * it.l + 4.0 * std::max(products, 0.0) + 4.0 + 10.0 / 32.0;
     cc.per_weight = 2.0;
     cc.per_high = 2.0 * it.l + 2.0;
-    cc.per_task = 84.0 + 2.0 * it.k;
+    cc.per_task = 8.0 + 2.0 * it.k;
+    cc.per_task_weighted = 4.0;
+    cc.per_task_whigh = 14.0;
     return cc;
 }
 
@@ -308,14 +316,19 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
         // and every task pays its chunk start-up and reductions.
         const CutCost k = cc ? *cc : forward_cut_cost(it);
         const int nd = (int)it.drad.size();
-        auto cost_rate = [&](int j, int64_t lj, double wrate) {
+        auto cost_rate = [&](int j, int64_t lj, double wrate, bool whigh) {
             const double ppt = k.per_term + k.per_weight * wrate;
-            const double ovh = (nd - j) * k.per_high + k.per_task + j * k.per_task_low;
+            const double ovh = (nd - j) * k.per_high + k.per_task + j * k.per_task_low +
+                               (wrate > 0.0 ? k.per_task_weighted : 0.0) +
+                               (whigh ? k.per_task_whigh : 0.0);
             const int64_t tasks = (it.T / lj + kWarp - 1) / kWarp;
             return tasks * ((double)lj * ppt + ovh);
         };
         auto cost_of = [&](int j, int64_t lj) {
-            return cost_rate(j, lj, weight_change_rate(it.drad, j));
+            bool whigh = false;
+            for (int d = j; d < nd; ++d)
+                whigh = whigh || it.drad[d] > 2;
+            return cost_rate(j, lj, weight_change_rate(it.drad, j), whigh);
         };
         int bestJ = J;
         int64_t bestL = L;
@@ -367,7 +380,10 @@ static void choose_chunks(ItemPlan& it, int log2_cap, int jmax = kMaxLowDigits,
                     --budget;
                     const int a2 = (!vals.empty() && vals[0] == 2) ? cur[0] : 0;
                     const double wr = (a2 == j) ? 0.0 : std::ldexp(1.0, -a2);
-                    const double c = cost_rate(j, lj, wr);
+                    bool whigh = !it.drad.empty() && it.drad.back() > kMaxLowRadix;
+                    for (size_t q = 0; q < vals.size(); ++q)
+                        whigh = whigh || (vals[q] > 2 && cur[q] < cnt[q]);
+                    const double c = cost_rate(j, lj, wr, whigh);
                     if (c < best * 0.999) {
                         best = c;
                         bestc = cur;
@@ -740,14 +756,19 @@ static int schedule_and_upload(pq_plan* P)
             instr_f += (double)tt * fwd_instr_per_term(it);
             flops_b += (double)tt * bwd_flops_per_term(it);
             // per task, every lane: L terms, the chunk start ((ndig - J) row
-            // updates of 2l), the chunk's fold and scaling (28) and the lane
-            // tree (56); per permanent with several tasks, the partials'
-            // double-double sum (14 per task and lane) and one more tree
+            // updates of 2l), the chunk's last folds (8, 12 when weighted) and
+            // the high-digit weight's product (14, when a high radix is above
+            // 2); the lane sum is integer work.  Per permanent with several
+            // tasks, the partials' double-double sum (14 per 32 tasks and lane)
+            bool whigh = false;
+            for (size_t d = it.J; d < it.drad.size(); ++d)
+                whigh = whigh || it.drad[d] > 2;
             const double lane = (double)it.L * fwd_instr_per_term(it) +
-                                2.0 * it.l * (double)((int)it.drow.size() - it.J) + 28.0 + 56.0;
+                                2.0 * it.l * (double)((int)it.drow.size() - it.J) +
+                                (it.weighted ? 12.0 : 8.0) + (whigh ? 14.0 : 0.0);
             instr_fx += (double)nt * 32.0 * lane;
             if (nt > 1)
-                instr_fx += 32.0 * (14.0 * (double)((nt + kWarp - 1) / kWarp) + 56.0);
+                instr_fx += 32.0 * 14.0 * (double)((nt + kWarp - 1) / kWarp);
         }
         if (slot < 0)
             return fail(PQ_ERR_UNSUPPORTED, "too many tasks");

@@ -85,7 +85,8 @@ def side_terms(m):
 
 @pytest.mark.parametrize("r,c", [([1] * 12, [1] * 12), ([2, 1, 3], [1, 1, 1, 1, 1, 1]),
                                  ([1, 1, 1, 1], [4]), ([2, 2, 2], [3, 3]), ([3], [3]),
-                                 ([0, 2, 0, 1], [1, 0, 2]), ([1] * 30, [1] * 30)])
+                                 ([0, 2, 0, 1], [1, 0, 2]), ([1] * 30, [1] * 30),
+                                 ([1], [1]), ([0, 1], [1, 0]), ([2], [1, 1])])
 def test_planner_side_choice_and_term_count(lib, r, c):
     rc, info = item_info(lib, r, c)
     assert rc == 0
