@@ -41,6 +41,7 @@
 
 #include "../../include/pq.h"
 #include "pq_device.cuh"
+#include "pq_fixsum.cuh"
 #include "pq_kernels.h"
 
 namespace pqi {
@@ -373,11 +374,9 @@ __device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, in
         fast_two_sum(ih, il, ih, il);
         dd_mul_d(rh, rl, whigh);
         dd_mul_d(ih, il, whigh);
-        res.rh = rh;
-        res.rl = rl;
-        res.ih = ih;
-        res.il = il;
-        res = warp_sum_dd2(res);
+        // the lanes' sums added exactly in integers (pq_fixsum.cuh)
+        warp_fix_sum(rh, rl, res.rh, res.rl);
+        warp_fix_sum(ih, il, res.ih, res.il);
     }
 
     auto finish = [&](dd2 v) {
@@ -420,7 +419,8 @@ __device__ void haf_task(const HafArgs& a, const Task& t, unsigned char* raw, in
         dd_add(tot.rh, tot.rl, __ldcg(pp + 0), __ldcg(pp + 1));
         dd_add(tot.ih, tot.il, __ldcg(pp + 2), __ldcg(pp + 3));
     }
-    tot = warp_sum_dd2(tot);
+    warp_fix_sum(tot.rh, tot.rl, tot.rh, tot.rl);
+    warp_fix_sum(tot.ih, tot.il, tot.ih, tot.il);
     if (lane == 0)
         finish(tot);
 }
