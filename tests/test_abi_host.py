@@ -252,3 +252,16 @@ def test_exact_warp_sum_drops_only_bits_far_below_the_largest(lib):
     assert rc == 0 and Fraction(float(out[0])) + Fraction(float(out[1])) == Fraction(-7, 2) + Fraction(2) ** -60
     assert fixsum(lib, [np.inf], [0.0])[0] == pq.PQ_ERR_ARG
     assert fixsum(lib, np.ones(33), np.zeros(33))[0] == pq.PQ_ERR_ARG
+
+
+def test_chunk_digits_fill_the_warp_tasks(lib):
+    """The batched cut may take any radices as a chunk's digits: rows
+    (2, 2, 2, 3, 3) against 12 single columns give Gray radices 2, 3, 3, 4, 4
+    (T = 288); the prefix cut (2, 3: chunks of 6) leaves 48 chunks, two warp
+    tasks with 16 idle lanes, while the chunk digits (3, 3) give 32 chunks of
+    9 terms, one full task."""
+    rc, info = item_info(lib, [2, 2, 2, 3, 3], [1] * 12)
+    assert rc == 0 and info.terms == 288
+    rad = list(info.radix[:info.ndig])
+    assert sorted(rad) == [2, 3, 3, 4, 4]
+    assert rad[:info.J] == [3, 3] and info.chunk_len == 9 and info.chunks == 32
