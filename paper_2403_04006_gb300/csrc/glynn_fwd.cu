@@ -20,9 +20,10 @@
 //     complex products for P(l) plus one per extra prefix, instead of n - 1;
 //     the last product is fused into the running sum (four DFMA);
 //   * the sign (-1)^step alternates, so pairs of terms are unrolled with the
-//     sign folded into the DFMA operands; binomial weights of low digits with
-//     radix > 2 scale one factor (two DMUL);
-//   * every 16 terms the FP64 running sum is folded into a double-double
+//     sign folded into the DFMA operands; the binomial weight of the low
+//     digits changes only when a digit of radix > 2 moves, so a run of equally
+//     weighted terms is summed unweighted and weighted once (two DFMA);
+//   * every 32 terms the FP64 running sum is folded into a double-double
 //     accumulator with TwoSum.
 // A warp task is up to 32 chunks of one permanent (one per lane).  The lanes'
 // sums are added exactly, in 128-bit integers (pq_fixsum.cuh), and the tasks
