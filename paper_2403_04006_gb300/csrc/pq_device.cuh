@@ -1,5 +1,5 @@
 // pq_device.cuh -- device helpers shared by the forward and backward kernels:
-// double-double accumulation, complex FP64 products, warp reductions, the
+// double-double accumulation, complex FP64 products, the
 // warp-uniform mixed-radix Gray walk and the per-task shared-memory staging.
 #pragma once
 #include <cuda_runtime.h>
@@ -64,12 +64,6 @@ __device__ __forceinline__ void dd_add(double& ah, double& al, double bh, double
     fast_two_sum(s, e, ah, al);
 }
 
-__device__ __forceinline__ void dd2_add(dd2& a, const dd2& b)
-{
-    dd_add(a.rh, a.rl, b.rh, b.rl);
-    dd_add(a.ih, a.il, b.ih, b.il);
-}
-
 // (h, l) * w for a double w
 __device__ __forceinline__ void dd_mul_d(double& h, double& l, double w)
 {
@@ -77,46 +71,6 @@ __device__ __forceinline__ void dd_mul_d(double& h, double& l, double w)
     double e = __fma_rn(h, w, -p);
     e = __fma_rn(l, w, e);
     fast_two_sum(p, e, h, l);
-}
-
-__device__ __forceinline__ dd2 shfl_down_dd2(const dd2& v, int off)
-{
-    dd2 r;
-    r.rh = __shfl_down_sync(0xffffffffu, v.rh, off);
-    r.rl = __shfl_down_sync(0xffffffffu, v.rl, off);
-    r.ih = __shfl_down_sync(0xffffffffu, v.ih, off);
-    r.il = __shfl_down_sync(0xffffffffu, v.il, off);
-    return r;
-}
-
-// Tree sum over the 32 lanes in a fixed order; lane 0 holds the result.
-// Each level adds the high parts with the ordered TwoSum and gathers the
-// exact error and both low parts into the low part (5 FP64 operations per
-// component instead of a renormalised double-double addition's 20); one
-// more ordered TwoSum at the end renormalises.  The low part collects at most
-// a few roundings of numbers 2^-53 smaller than the high part, so the sum
-// keeps double-double accuracy.
-__device__ __forceinline__ dd2 warp_sum_dd2(dd2 v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const dd2 o = shfl_down_dd2(v, off);
-        double s, e;
-        two_sum_ord(v.rh, o.rh, s, e);
-        v.rh = s;
-        v.rl = __dadd_rn(__dadd_rn(v.rl, o.rl), e);
-        two_sum_ord(v.ih, o.ih, s, e);
-        v.ih = s;
-        v.il = __dadd_rn(__dadd_rn(v.il, o.il), e);
-    }
-    double s, e;
-    two_sum_ord(v.rh, v.rl, s, e);
-    v.rh = s;
-    v.rl = e;
-    two_sum_ord(v.ih, v.il, s, e);
-    v.ih = s;
-    v.il = e;
-    return v;
 }
 
 // ---------------------------------------------------------------- complex FP64
