@@ -193,7 +193,7 @@ def profiled_traffic():
     return float(b.group(1))
 
 
-PROFILE_CASES = ("ragged-backward", "ragged4096-backward", "hafnian-2x", "loop-hafnian-2x",
+PROFILE_CASES = ("ragged-backward", "ragged4096-backward", "bs-m24", "hafnian-2x", "loop-hafnian-2x",
                  "gradient-m16", "fp64-sweep")
 
 
@@ -695,6 +695,17 @@ def bench_case(args, dev):
         terms_of = lambda: plan.stats()["terms"]  # noqa: E731
         if args.workload == "ragged4096-backward":
             desc = desc.replace("(profiling case)", "backward (profiling case)")
+    elif args.workload == "bs-m24":
+        U3, s3, t3 = W.bs_batched()
+        Ud3, sd3, td3 = (torch.from_numpy(x).to(dev) for x in (U3, s3, t3))
+        plan3 = api.Plan.for_bs(24, s3, t3, use_graph=True)
+
+        def op():
+            api.bs_probs(Ud3, sd3, td3, plan3, stream=stream)
+        terms_of = lambda: plan3.stats()["terms"]  # noqa: E731
+        extra = {"column_sums": plan3.stats()["column_sums"]}
+        desc = ("boson sampling m = 24, 12 photons in modes 0..11, 4096 output patterns, "
+                "batched plan (profiling case)")
     elif args.workload == "gradient-m16":
         th, ph, s5, t5 = W.gradient_workload()
         thd = torch.from_numpy(th).to(dev).requires_grad_(True)
