@@ -152,9 +152,22 @@ __host__ __device__ __forceinline__ void fix_to_dd(fix128 v, int emax, double& h
 
 #ifdef __CUDACC__
 // Exact sum of hi + lo over the 32 lanes of a warp (all lanes call it); every
-// lane receives the sum as a double-double.
+// lane receives the sum as a double-double.  A non-finite value anywhere in
+// the warp (an overflowing input) is summed in plain FP64 instead, so that
+// infinities and NaNs reach the output as they would through FP64 addition.
 __device__ __forceinline__ void warp_fix_sum(double hi, double lo, double& shi, double& slo)
 {
+    const bool nonfinite = ((fix_bits(hi) >> 52) & 0x7ff) == 0x7ff ||
+                           ((fix_bits(lo) >> 52) & 0x7ff) == 0x7ff;
+    if (__any_sync(0xffffffffu, nonfinite)) {
+        double t = hi + lo;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            t += __shfl_xor_sync(0xffffffffu, t, off);
+        shi = t;
+        slo = 0.0;
+        return;
+    }
     const int e = max(fix_exp(hi), fix_exp(lo));
     const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
     const fix128 v = fix_of(hi, emax) + fix_of(lo, emax);

@@ -710,3 +710,19 @@ def test_sharded_plan_misuse(dev):
         with pytest.raises(pq.PQError) as e:
             call()
         assert e.value.code == code
+
+
+@pytest.mark.parametrize("method", ["batched", "plain"])
+def test_overflowing_permanent_is_not_finite(dev, method):
+    """A permanent whose terms overflow FP64 (1 x 1 base 1e200 repeated twice:
+    per = 2 * 1e400) comes out infinite or NaN, as FP64 arithmetic gives it,
+    not as a finite number made up by the integer lane sum; the permanents
+    beside it in the batch are unaffected."""
+    rng = np.random.default_rng(77)
+    items = random_items(6, 2, 8, rng) + [(np.array([[1e200 + 0j]]), [2], [2])]
+    pb = W.pack_batch(items)
+    got = api.permanent_batched(api.DeviceBatch(pb, dev), api.Plan.for_batch(pb, method=method))
+    got = got.cpu().numpy()
+    assert not np.isfinite(got[-1])
+    ref = oracle_items(items[:-1])
+    assert rel_err(got[:-1], ref).max() <= TOL
