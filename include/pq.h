@@ -380,7 +380,11 @@ int pq_loop_hafnian_repeated(const pq_c128* mats, const pq_c128* gamma, const in
  * whole batch with those picks and with the chunking the plan had, and keeps
  * the picks -- in the plan and in the process-wide tuning table used by later
  * plans -- only if they are at least 1% faster.  Otherwise the plan and the
- * table stay as they were.  Synchronises `stream`.  b is the batch the plan
+ * table stay as they were.  A plan whose column sums the planner put in
+ * registers (column_sums PQ_SUMS_AUTO, one column class) is then timed with
+ * them in shared memory as well, and keeps shared memory if that is at least
+ * 1% faster (pq_plan_get_stats reports the choice).  Synchronises `stream`.
+ * b is the batch the plan
  * was made for (device descriptor); for a boson-sampling plan pass b = NULL
  * and U (device) instead.  If re-planning fails (PQ_ERR_NOMEM, PQ_ERR_CUDA)
  * and the plan cannot be restored, later runs of it return PQ_ERR_STATE. */

@@ -359,10 +359,32 @@ def test_autotune_then_parity(dev):
     U, s, t = W.bs_batched()
     Ud, sd, td = (torch.from_numpy(x).to(dev) for x in (U, s, t))
     plan = api.Plan.for_bs(24, s, t)
+    assert plan.stats()["column_sums"] == "registers"  # one column class
     plan.autotune(U=Ud)
+    assert plan.stats()["column_sums"] in ("registers", "shared")  # the faster one
     p, a = api.bs_probs(Ud, sd, td, plan)
     p_ref, a_ref = O.bs_probs(U, s, t, gold=True)
     assert rel_err(a.cpu().numpy(), a_ref).max() <= TOL
+
+
+def test_autotune_chooses_the_faster_column_sums_and_keeps_parity(dev):
+    """A batch of one column class (collision-free n = 12): the autotuner
+    times the plan with column sums in registers and in shared memory, keeps
+    one, and the result still matches the oracle; forcing either form in
+    the options keeps it through tuning."""
+    A = W.single_large(30)
+    items = [(A[i:i + 12, :12], [1] * 12, [1] * 12) for i in range(0, 18, 2)] * 64
+    pb = W.pack_batch(items)
+    db = api.DeviceBatch(pb, dev)
+    ref = oracle_items(items[:9])
+    for cs in ("auto", "shared", "registers"):
+        plan = api.Plan.for_batch(pb, column_sums=cs)
+        plan.autotune(db)
+        form = plan.stats()["column_sums"]
+        assert form == ("registers" if cs == "registers" else "shared") or cs == "auto"
+        got = api.permanent_batched(db, plan).cpu().numpy()
+        assert rel_err(got[:9], ref).max() <= TOL
+        assert np.array_equal(got.view(np.float64), np.tile(got[:9], 64).view(np.float64))
 
 
 # ------------------------------------------------------------------ backward
