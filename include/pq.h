@@ -566,6 +566,14 @@ int pq_plan_item_info(int32_t k, int32_t l, const int32_t* row_mult, const int32
  * pointer or a value that is not finite. */
 int pq_fixsum_host(const double* hi, const double* lo, int32_t n, double* out);
 
+/* The same warp sum run by one warp on the device (a test of the device
+ * code): hi[n], lo[n] device arrays, n <= 32; out: device array of 64
+ * doubles, lane q's copy of the sum in out[2q], out[2q + 1].  Asynchronous
+ * on stream.  A non-finite input makes the warp add in plain FP64 (the
+ * result is then not finite).  PQ_ERR_ARG: n outside [0, 32] or a null
+ * pointer; PQ_ERR_CUDA: the launch failed. */
+int pq_fixsum_device(const double* hi, const double* lo, int32_t n, double* out, void* stream);
+
 /* Run the kernels' warp-uniform Gray walk on the host: ndig <= 15 digits with
  * radix[d] in [2, 15]; for `steps` steps writes the digit that changes and
  * its direction (+1 / -1) to host arrays digit[steps], dir[steps]. */

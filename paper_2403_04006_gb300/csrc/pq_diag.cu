@@ -61,3 +61,25 @@ extern "C" int pq_fixsum_host(const double* hi, const double* lo, int32_t n, dou
     pqi::fix_to_dd(pqi::fix_from_limbs(sum, top), emax, out[0], out[1]);
     return PQ_OK;
 }
+
+// The same sum on the device, by one warp: lane q adds hi[q] + lo[q] (zero
+// beyond n) and writes its copy of the result to out[2q], out[2q + 1].
+__global__ void fixsum_probe_kernel(const double* hi, const double* lo, int n, double* out)
+{
+    const int lane = threadIdx.x;
+    const double h = lane < n ? hi[lane] : 0.0;
+    const double l = lane < n ? lo[lane] : 0.0;
+    double sh, sl;
+    pqi::warp_fix_sum(h, l, sh, sl);
+    out[2 * lane] = sh;
+    out[2 * lane + 1] = sl;
+}
+
+extern "C" int pq_fixsum_device(const double* hi, const double* lo, int32_t n, double* out,
+                                void* stream)
+{
+    if (n < 0 || n > 32 || !out || (n > 0 && (!hi || !lo)))
+        return PQ_ERR_ARG;
+    fixsum_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(hi, lo, n, out);
+    return cudaGetLastError() == cudaSuccess ? PQ_OK : PQ_ERR_CUDA;
+}

@@ -101,6 +101,7 @@ _SIGNATURES = {
     "pq_plan_item_info": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "pq_gray_walk": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     "pq_fixsum_host": (_i32, [_vp, _vp, _i32, _vp]),
+    "pq_fixsum_device": (_i32, [_vp, _vp, _i32, _vp, _vp]),
     "pq_loop_poly_factors": (_i32, [_i32, _vp]),
     "pq_combine_partials": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp]),
     "pq_combine_partials_host": (_i32, [_vp, _i32, _i64, _vp, _vp]),
