@@ -1362,9 +1362,12 @@ extern "C" int pq_probe_fp64_peak(int64_t iters, double* flops_per_s, double* ms
 }
 
 // ---------------------------------------------------------------- backward
-// The backward pass keeps per-lane running sums for the low digits in shared
-// memory, so it uses its own, shorter chunks (at most kBwdMaxLowDigits low
-// digits, about 2^5 terms).
+// The backward pass keeps one row of per-lane corrections for each low digit
+// in shared memory, so it uses its own chunks: at most kBwdMaxLowDigits low
+// digits and 2^kBwdChunkLog2 terms (radices 3 and 4 among the chunk's digits
+// make chunks longer than 2^J; on the ragged batch caps of 2^4 .. 2^8 terms
+// took 78.2, 73.2, 71.1, 70.6 and 71.7 ms: fewer chunk starts, each of which
+// costs 2l per high digit).
 // Product-column bounds of the backward launch classes: every permanent runs
 // in the launch of the smallest bound that holds its l, so its per-lane
 // workspace (column sums, accumulators, prefixes, corrections) is sized for
@@ -1450,19 +1453,54 @@ static int ensure_backward(pq_plan* P)
     // can differ from the forward's: the backward reads a copy of the
     // metadata pool whose digit sections follow its order.
     std::vector<int32_t> meta_bwd = P->meta_h;
+    // per term as glynn_bwd.cu counts it; a chunk start 2l per high digit;
+    // per task the staging (k), the lane contraction (2l per low digit, about
+    // 2kl) and the gradient write
+    auto bwd_cut_cost = [&](const ItemPlan& it, const BwdClass& C) {
+        CutCost bc;
+        bc.per_term = bwd_instr_per_term(it, C.reg != 0);
+        bc.per_high = 2.0 * it.l;
+        bc.per_task = it.k + 66.0 * it.k * it.l / 32.0;
+        bc.per_task_low = 2.0 * it.l;
+        return bc;
+    };
+    // Chunk cap of each class.  Long chunks start less often, but a class
+    // with few permanents then has too few, too long warp tasks for its
+    // launch (4096 permanents of the ragged recipe: 5.5 ms with caps of 2^4
+    // terms, 7.4 ms with 2^7): as for the forward, the cap is lowered from
+    // 2^kBwdChunkLog2 towards 2^4 until the longest task is at most half of a
+    // resident warp's average share of the class's work.
+    std::vector<int> cls_cap(ncls, kBwdChunkLog2);
+    for (int c = 0; c < ncls; ++c) {
+        if (!cls_used[c])
+            continue;
+        const BwdClass& C = cls[c];
+        const double warps = (double)C.blocks * C.wpb;
+        for (int cap = kBwdChunkLog2; cap >= 4; --cap) {
+            double total = 0.0, longest = 0.0;
+            for (int64_t p = 0; p < np; ++p) {
+                if (P->bwd_class_of[p] != c || items[p].trivial)
+                    continue;
+                ItemPlan it = items[p];
+                const CutCost bc = bwd_cut_cost(it, C);
+                choose_chunks(it, cap, std::max(C.jb, 1), kWarp, true, &bc);
+                const double task = (double)it.L * bc.per_term +
+                                    ((int)it.drad.size() - it.J) * bc.per_high + bc.per_task +
+                                    it.J * bc.per_task_low;
+                total += task * (double)((it.nchunks + kWarp - 1) / kWarp);
+                longest = std::max(longest, task);
+            }
+            cls_cap[c] = cap;
+            if (total <= 0.0 || longest <= 0.5 * total / warps)
+                break;
+        }
+    }
     for (int64_t p = 0; p < np; ++p) {
         ItemPlan& it = items[p];
         const BwdClass& C = cls[P->bwd_class_of[p]];
         if (!it.trivial) {
-            // per term as glynn_bwd.cu counts it; a chunk start 2l per high
-            // digit; per task the staging (k), the lane contraction (2l per
-            // low digit, about 2kl) and the gradient write
-            CutCost bc;
-            bc.per_term = bwd_instr_per_term(it, C.reg != 0);
-            bc.per_high = 2.0 * it.l;
-            bc.per_task = it.k + 66.0 * it.k * it.l / 32.0;
-            bc.per_task_low = 2.0 * it.l;
-            choose_chunks(it, kBwdChunkLog2, std::max(C.jb, 1), kWarp, true, &bc);
+            const CutCost bc = bwd_cut_cost(it, C);
+            choose_chunks(it, cls_cap[P->bwd_class_of[p]], std::max(C.jb, 1), kWarp, true, &bc);
             const PermDesc& Df = P->desc_h[p];
             const int nd = (int)it.drow.size();
             int32_t* dig = meta_bwd.data() + Df.meta + 2 * Df.k + 2 * Df.l;

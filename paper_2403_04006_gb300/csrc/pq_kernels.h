@@ -99,7 +99,7 @@ struct BwdArgs {
 };
 int bwd_smem_bytes_for(int kmax, int lmax, int jb, int n2);
 constexpr int kBwdMaxLowDigits = 4;  // low digits the backward workspace holds
-constexpr int kBwdChunkLog2 = 4;     // backward chunks of at most 2^4 terms
+constexpr int kBwdChunkLog2 = 7;     // backward chunks of at most 2^7 terms
 cudaError_t bwd_prepare(int lmax, int smem_bytes);
 cudaError_t bwd_launch_persistent(int ld, const BwdArgs& a, int64_t t_begin, int64_t t_end,
                                   int kmax, int jb, int n2, int blocks, int wpb, cudaStream_t st);
