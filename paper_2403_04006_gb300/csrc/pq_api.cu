@@ -1470,13 +1470,17 @@ static int ensure_backward(pq_plan* P)
     // terms, 7.4 ms with 2^7): as for the forward, the cap is lowered from
     // 2^kBwdChunkLog2 towards 2^4 until the longest task is at most half of a
     // resident warp's average share of the class's work.
-    std::vector<int> cls_cap(ncls, kBwdChunkLog2);
-    for (int c = 0; c < ncls; ++c) {
+    // The plain method launches one permanent at a time and needs its many
+    // short chunks to fill the GPU: it keeps caps of 2^4 terms (the ragged
+    // batch's plain backward took 5.9 s with them, 17.7 s with 2^7).
+    const int cap0 = P->opts.method == PQ_METHOD_PLAIN ? 4 : kBwdChunkLog2;
+    std::vector<int> cls_cap(ncls, cap0);
+    for (int c = 0; c < ncls && cap0 > 4; ++c) {
         if (!cls_used[c])
             continue;
         const BwdClass& C = cls[c];
         const double warps = (double)C.blocks * C.wpb;
-        for (int cap = kBwdChunkLog2; cap >= 4; --cap) {
+        for (int cap = cap0; cap >= 4; --cap) {
             double total = 0.0, longest = 0.0;
             for (int64_t p = 0; p < np; ++p) {
                 if (P->bwd_class_of[p] != c || items[p].trivial)
