@@ -11,9 +11,12 @@ the scale of the cancellation).  Wherever that bound is below the tolerance
 -- a cancellation ratio sum |terms| / |value| of at most 1e4, which holds for
 every item of the ragged batches and the (2, ..., 2) shapes here (the largest
 ratio is about 600) -- the check is relative: |gpu - oracle| <= 1e-10 |oracle|.
-Exact zeros (odd N) must come out exactly zero.  Only the block-diagonal
-N = 32 case, whose full sum the oracle cannot evaluate and whose ratio is
-about 3e4, is bounded against the scale instead.
+Exact zeros (odd N) must come out exactly zero.  The block-diagonal N = 32
+case, whose full sum the oracle cannot evaluate and whose ratio is about 2e4,
+is checked relative to the product of its blocks' hafnians (each block's
+ratio is below 1e3, so that product is accurate to about 1e-12); the lanes'
+sums are exact integer sums, and the GPU's error there measured 3e-13 to
+4e-13 relative.
 """
 import math
 
@@ -125,9 +128,13 @@ def test_block_diagonal_factorises_at_large_size(dev, loop):
     else:
         (h1, s1), (h2, s2) = O.haf_grouped(B1, r1, info=True), O.haf_grouped(B2, r2, info=True)
     ref = h1 * h2
-    # The full sum's term-magnitude scale, sampled on the CPU for these
-    # inputs, is about 1.4 s1 s2 (and 3e4 |ref|): bound at 1e-9 s1 s2.
-    assert abs(got - ref) <= 1e-9 * max(abs(ref), s1 * s2), (got, ref, s1 * s2)
+    # The reference is a product of two k = 8 sums whose own cancellation is
+    # mild (term scale over value below 1e3 each), so it holds to about
+    # 1e-12 relative; the GPU's whole N = 32 sum cancels far more (term scale
+    # about 2e4 |ref|) and is held to the relative tolerance of the other
+    # parity tests (measured on a GB300: 3e-13 and 4e-13).
+    assert s1 < 1e3 * abs(h1) and s2 < 1e3 * abs(h2), (s1 / abs(h1), s2 / abs(h2))
+    assert abs(got - ref) <= TOL * abs(ref), (got, ref, abs(got - ref) / abs(ref))
 
 
 def test_edge_cases(dev):
